@@ -1,0 +1,237 @@
+"""FP64 CPU oracle for the even-odd staggered operator and CG (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the CUDA product path
+never does.  The arithmetic lives in ``stag_oracle.c`` (plain C, FP64, no FMA
+contraction); this module only compiles it with gcc and marshals numpy arrays.
+
+Layouts (complex128 numpy arrays, C order):
+  links       (4, V, 3, 3)   direction, lexicographic site (x fastest), row, col
+  full vector (V, 3)
+  cb vector   (V/2, 3)       checkerboard index = lex // 2 of the sites of one parity
+with dims = (Lx, Ly, Lz, Lt).
+
+Parity notes: ``quantize_vectors``/``round_links`` are pinned to numpy's
+float16 and torch's bfloat16 rounding; the operator, CG and force are pinned by
+the free-field closed form, anti-Hermiticity, gauge covariance, translation
+invariance, dense brute force and central finite differences (tests/).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stag_oracle.c")
+_LIB = os.path.join(_HERE, "libstag_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (once; again when the source is newer)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(path):
+    """Load a compiled oracle library from `path` and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    L = ctypes.c_long
+    sig = {
+        "orc_dslash_full": (None, [P, I, P, P, P]),
+        "orc_gather_parity": (None, [P, I, P, P]),
+        "orc_scatter_parity": (None, [P, I, P, P]),
+        "orc_dslash_oe": (None, [P, I, P, P, P]),
+        "orc_dslash_eo": (None, [P, I, P, P, P]),
+        "orc_mdagm": (None, [P, I, P, D, P, P]),
+        "orc_true_residual": (D, [P, I, P, D, P, P]),
+        "orc_cg": (I, [P, I, P, D, P, P, D, I, P, P]),
+        "orc_round_format": (D, [D, I, I]),
+        "orc_quantize_vectors": (None, [I, L, P, P]),
+        "orc_round_links": (None, [I, L, P, P]),
+        "orc_force_K": (None, [P, I, P, P, P]),
+        "orc_force_lie": (None, [L, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+class using:
+    """Context manager: route this module's functions to another compiled copy
+    of the oracle (used by the tests that plant mistakes in a copy)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = _bind(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(_LIB)
+    return _lib
+
+
+def _dims(L):
+    a = np.ascontiguousarray(np.asarray(L, dtype=np.int32))
+    assert a.shape == (4,)
+    return a
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def volume(L):
+    return int(np.prod(np.asarray(L, dtype=np.int64)))
+
+
+def dslash_full(L, links, v, antiperiodic=True):
+    """D v on the full lattice."""
+    lib = _load()
+    d, U, x = _dims(L), _c128(links), _c128(v)
+    out = np.empty_like(x)
+    lib.orc_dslash_full(_p(d), int(antiperiodic), _p(U), _p(x), _p(out))
+    return out
+
+
+def gather_parity(L, par, full):
+    lib = _load()
+    d, f = _dims(L), _c128(full)
+    out = np.empty((volume(L) // 2, 3), np.complex128)
+    lib.orc_gather_parity(_p(d), int(par), _p(f), _p(out))
+    return out
+
+
+def scatter_parity(L, par, cb):
+    lib = _load()
+    d, c = _dims(L), _c128(cb)
+    out = np.empty((volume(L), 3), np.complex128)
+    lib.orc_scatter_parity(_p(d), int(par), _p(c), _p(out))
+    return out
+
+
+def dslash_oe(L, links, v_even, antiperiodic=True):
+    """D_oe v: even-site input, odd-site output."""
+    lib = _load()
+    d, U, x = _dims(L), _c128(links), _c128(v_even)
+    out = np.empty_like(x)
+    lib.orc_dslash_oe(_p(d), int(antiperiodic), _p(U), _p(x), _p(out))
+    return out
+
+
+def dslash_eo(L, links, v_odd, antiperiodic=True):
+    """D_eo v: odd-site input, even-site output."""
+    lib = _load()
+    d, U, x = _dims(L), _c128(links), _c128(v_odd)
+    out = np.empty_like(x)
+    lib.orc_dslash_eo(_p(d), int(antiperiodic), _p(U), _p(x), _p(out))
+    return out
+
+
+def mdagm(L, links, mass, v_even, antiperiodic=True):
+    """(4 m^2 - D_eo D_oe) v on even sites."""
+    lib = _load()
+    d, U, x = _dims(L), _c128(links), _c128(v_even)
+    out = np.empty_like(x)
+    lib.orc_mdagm(_p(d), int(antiperiodic), _p(U), float(mass), _p(x), _p(out))
+    return out
+
+
+def true_residual(L, links, mass, b, x, antiperiodic=True):
+    """||b - A x|| / ||b|| in FP64."""
+    lib = _load()
+    d, U, bb, xx = _dims(L), _c128(links), _c128(b), _c128(x)
+    return float(lib.orc_true_residual(_p(d), int(antiperiodic), _p(U), float(mass),
+                                       _p(bb), _p(xx)))
+
+
+def cg(L, links, mass, b, tol=1e-10, maxiter=100000, antiperiodic=True):
+    """Plain FP64 CG on A = M^dag M.  Returns (x, status, iters, true_res)."""
+    lib = _load()
+    d, U, bb = _dims(L), _c128(links), _c128(b)
+    x = np.empty_like(bb)
+    it = ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    st = lib.orc_cg(_p(d), int(antiperiodic), _p(U), float(mass), _p(bb), _p(x), float(tol),
+                    int(maxiter), ctypes.byref(it), ctypes.byref(tr))
+    return x, int(st), int(it.value), float(tr.value)
+
+
+def round_format(v, mant_bits, emin):
+    return float(_load().orc_round_format(float(v), int(mant_bits), int(emin)))
+
+
+PREC_FP32, PREC_FP16, PREC_BF16 = 1, 2, 3
+
+
+def quantize_vectors(prec, v):
+    """Values a (n, 3) complex vector holds after storage at `prec` (1/2/3)."""
+    lib = _load()
+    x = _c128(v)
+    out = np.empty_like(x)
+    lib.orc_quantize_vectors(int(prec), x.shape[0], _p(x), _p(out))
+    return out
+
+
+def round_links(prec, links):
+    """Values link elements hold after storage at `prec` (1/2/3)."""
+    lib = _load()
+    x = _c128(links)
+    out = np.empty_like(x)
+    lib.orc_round_links(int(prec), x.size * 2, _p(x), _p(out))
+    return out
+
+
+def force_K(L, links, x_even, antiperiodic=True):
+    """K_mu(x) with dS = Re Tr(K dU) for S = phi^dag A^{-1} phi, X = A^{-1} phi."""
+    lib = _load()
+    d, U, X = _dims(L), _c128(links), _c128(x_even)
+    K = np.empty((4, volume(L), 3, 3), np.complex128)
+    lib.orc_force_K(_p(d), int(antiperiodic), _p(U), _p(X), _p(K))
+    return K
+
+
+def force_lie(links, K):
+    """f_a = Re Tr(i T_a U K), T_a = lambda_a/2; shape (4, V, 8)."""
+    lib = _load()
+    U, KK = _c128(links), _c128(K)
+    n = U.size // 9
+    f = np.empty(U.shape[:-2] + (8,), np.float64)
+    lib.orc_force_lie(n, _p(U), _p(KK), _p(f))
+    return f

@@ -1,0 +1,459 @@
+/*
+ * stag_oracle.c -- plain, slow, FP64 CPU oracle for the even-odd preconditioned
+ * staggered operator and the conjugate-gradient solve built on it.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  The CUDA product
+ * path shares no code, header, table or helper with it.
+ *
+ * What it follows.  Sec. 3 ("CG Performance") of the paper names the method:
+ * a mixed-precision conjugate-gradient inverter for HYP-smeared staggered
+ * quarks on a 20^3 x 64 lattice.  The paper never writes the operator down, so
+ * the oracle states the standard one-link staggered operator with these
+ * conventions (each pinned by a test against a closed form or an invariant):
+ *
+ *   sites x = (x0,x1,x2,x3) = (x,y,z,t), lexicographic index with x fastest;
+ *   parity(x) = (x0+x1+x2+x3) mod 2, even = 0;
+ *   checkerboard index of a site = lex / 2 (needs L0 even);
+ *   staggered phase  eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1})   (eta_0 = 1);
+ *   boundary sign    b_mu(x)   = -1 if mu = t, the antiperiodic flag is set and
+ *                                x_t = L_t - 1, else +1;
+ *   (D psi)(x) = sum_mu [ eta_mu(x) b_mu(x) U_mu(x) psi(x+mu)
+ *                       - eta_mu(x-mu) b_mu(x-mu) U_mu(x-mu)^dagger psi(x-mu) ]
+ *                with periodic index wrap; both hops are ACCUMULATED (on a
+ *                length-2 direction x+mu and x-mu are the same site);
+ *   D_oe = odd rows, even columns of D;  D_eo = even rows, odd columns;
+ *   A = M^dagger M on even sites = 4 m^2 - D_eo D_oe   (Hermitian, >= 4m^2).
+ *
+ * Memory layouts (all FP64, complex = (re, im) pairs):
+ *   links  [4][V][3][3]  (direction, lexicographic site, row, column)
+ *   full-lattice vector [V][3]; checkerboard vector [V/2][3] (cb index order).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so that
+ * x86-64 and aarch64 hosts produce identical results).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    double re, im;
+} cplx;
+
+static cplx c_add(cplx a, cplx b) { cplx r = {a.re + b.re, a.im + b.im}; return r; }
+static cplx c_sub(cplx a, cplx b) { cplx r = {a.re - b.re, a.im - b.im}; return r; }
+static cplx c_mul(cplx a, cplx b)
+{
+    cplx r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+    return r;
+}
+static cplx c_conj(cplx a) { cplx r = {a.re, -a.im}; return r; }
+static cplx c_scale(double s, cplx a) { cplx r = {s * a.re, s * a.im}; return r; }
+
+/* ------------------------------------------------------------------ */
+/* lattice geometry                                                    */
+/* ------------------------------------------------------------------ */
+
+static long volume(const int L[4]) { return (long)L[0] * L[1] * L[2] * L[3]; }
+
+static long lex_of(const int L[4], const int x[4])
+{
+    return x[0] + (long)L[0] * (x[1] + (long)L[1] * (x[2] + (long)L[2] * x[3]));
+}
+
+static void coords_of(const int L[4], long i, int x[4])
+{
+    x[0] = (int)(i % L[0]); i /= L[0];
+    x[1] = (int)(i % L[1]); i /= L[1];
+    x[2] = (int)(i % L[2]); i /= L[2];
+    x[3] = (int)i;
+}
+
+static int parity_of(const int x[4]) { return (x[0] + x[1] + x[2] + x[3]) & 1; }
+
+/* staggered phase eta_mu(x) = (-1)^(sum_{nu<mu} x_nu) */
+static int eta(int mu, const int x[4])
+{
+    int s = 0;
+    for (int nu = 0; nu < mu; ++nu) s += x[nu];
+    return (s & 1) ? -1 : 1;
+}
+
+/* boundary sign of the link U_mu(x): antiperiodic in t */
+static int bsign(int mu, const int x[4], const int L[4], int antiperiodic)
+{
+    return (antiperiodic && mu == 3 && x[3] == L[3] - 1) ? -1 : 1;
+}
+
+static const cplx *link_at(const cplx *U, long V, int mu, long site)
+{
+    return U + ((long)mu * V + site) * 9;
+}
+
+/* ------------------------------------------------------------------ */
+/* the staggered operator on the full lattice                          */
+/* ------------------------------------------------------------------ */
+
+/* out = D in (full lattice).  Direct transcription of the definition above. */
+void orc_dslash_full(const int L[4], int antiperiodic, const double *Ud,
+                     const double *ind, double *outd)
+{
+    const cplx *U = (const cplx *)Ud;
+    const cplx *in = (const cplx *)ind;
+    cplx *out = (cplx *)outd;
+    long V = volume(L);
+    for (long i = 0; i < V; ++i) {
+        int x[4];
+        coords_of(L, i, x);
+        cplx acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int mu = 0; mu < 4; ++mu) {
+            int xf[4] = {x[0], x[1], x[2], x[3]};
+            int xb[4] = {x[0], x[1], x[2], x[3]};
+            xf[mu] = (x[mu] + 1) % L[mu];
+            xb[mu] = (x[mu] - 1 + L[mu]) % L[mu];
+            long jf = lex_of(L, xf), jb = lex_of(L, xb);
+
+            /* forward hop: + eta_mu(x) b_mu(x) U_mu(x) in(x+mu) */
+            double sf = (double)(eta(mu, x) * bsign(mu, x, L, antiperiodic));
+            const cplx *Uf = link_at(U, V, mu, i);
+            for (int a = 0; a < 3; ++a) {
+                cplx h = {0, 0};
+                for (int b = 0; b < 3; ++b) h = c_add(h, c_mul(Uf[a * 3 + b], in[jf * 3 + b]));
+                acc[a] = c_add(acc[a], c_scale(sf, h));
+            }
+            /* backward hop: - eta_mu(x-mu) b_mu(x-mu) U_mu(x-mu)^dagger in(x-mu) */
+            double sb = (double)(eta(mu, xb) * bsign(mu, xb, L, antiperiodic));
+            const cplx *Ub = link_at(U, V, mu, jb);
+            for (int a = 0; a < 3; ++a) {
+                cplx h = {0, 0};
+                for (int b = 0; b < 3; ++b) h = c_add(h, c_mul(c_conj(Ub[b * 3 + a]), in[jb * 3 + b]));
+                acc[a] = c_sub(acc[a], c_scale(sb, h));
+            }
+        }
+        for (int a = 0; a < 3; ++a) out[i * 3 + a] = acc[a];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* checkerboard (even/odd) views                                       */
+/* ------------------------------------------------------------------ */
+
+/* full[V][3] -> cb[V/2][3] for the sites of the given parity (cb = lex/2) */
+void orc_gather_parity(const int L[4], int par, const double *fulld, double *cbd)
+{
+    const cplx *full = (const cplx *)fulld;
+    cplx *cb = (cplx *)cbd;
+    long V = volume(L);
+    for (long i = 0; i < V; ++i) {
+        int x[4];
+        coords_of(L, i, x);
+        if (parity_of(x) != par) continue;
+        for (int a = 0; a < 3; ++a) cb[(i / 2) * 3 + a] = full[i * 3 + a];
+    }
+}
+
+/* cb[V/2][3] -> full[V][3], zero on the other parity */
+void orc_scatter_parity(const int L[4], int par, const double *cbd, double *fulld)
+{
+    const cplx *cb = (const cplx *)cbd;
+    cplx *full = (cplx *)fulld;
+    long V = volume(L);
+    for (long i = 0; i < V; ++i) {
+        int x[4];
+        coords_of(L, i, x);
+        for (int a = 0; a < 3; ++a) {
+            cplx z = {0, 0};
+            full[i * 3 + a] = (parity_of(x) == par) ? cb[(i / 2) * 3 + a] : z;
+        }
+    }
+}
+
+/* out_par = (D restricted to rows of parity `out_par`, columns of the other parity) in */
+static void dslash_block(const int L[4], int antiperiodic, const double *U, int out_par,
+                         const double *in_cb, double *out_cb)
+{
+    long V = volume(L);
+    double *full_in = (double *)malloc(sizeof(double) * 6 * V);
+    double *full_out = (double *)malloc(sizeof(double) * 6 * V);
+    orc_scatter_parity(L, 1 - out_par, in_cb, full_in);
+    orc_dslash_full(L, antiperiodic, U, full_in, full_out);
+    orc_gather_parity(L, out_par, full_out, out_cb);
+    free(full_in);
+    free(full_out);
+}
+
+/* out_odd = D_oe in_even */
+void orc_dslash_oe(const int L[4], int antiperiodic, const double *U, const double *in_even,
+                   double *out_odd)
+{
+    dslash_block(L, antiperiodic, U, 1, in_even, out_odd);
+}
+
+/* out_even = D_eo in_odd */
+void orc_dslash_eo(const int L[4], int antiperiodic, const double *U, const double *in_odd,
+                   double *out_even)
+{
+    dslash_block(L, antiperiodic, U, 0, in_odd, out_even);
+}
+
+/* out_even = (4 m^2 - D_eo D_oe) in_even */
+void orc_mdagm(const int L[4], int antiperiodic, const double *U, double mass,
+               const double *in_even, double *out_even)
+{
+    long Ve = volume(L) / 2;
+    double *t = (double *)malloc(sizeof(double) * 6 * Ve);
+    orc_dslash_oe(L, antiperiodic, U, in_even, t);
+    orc_dslash_eo(L, antiperiodic, U, t, out_even);
+    double m4 = 4.0 * mass * mass;
+    for (long k = 0; k < 6 * Ve; ++k) out_even[k] = m4 * in_even[k] - out_even[k];
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* plain FP64 conjugate gradient on A = M^dagger M (even sites)        */
+/* ------------------------------------------------------------------ */
+
+/* <a,b> = sum conj(a) b, real part */
+static double re_dot(long n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long k = 0; k < n; ++k) s += a[k] * b[k]; /* pairs (re,im): re*re + im*im */
+    return s;
+}
+
+/* ||b - A x||_2 / ||b||_2, recomputed in FP64 (0 when b = 0 and x = 0) */
+double orc_true_residual(const int L[4], int antiperiodic, const double *U, double mass,
+                         const double *b, const double *x)
+{
+    long n = 6 * (volume(L) / 2);
+    double *Ax = (double *)malloc(sizeof(double) * n);
+    orc_mdagm(L, antiperiodic, U, mass, x, Ax);
+    double rr = 0.0, bb = 0.0;
+    for (long k = 0; k < n; ++k) {
+        double d = b[k] - Ax[k];
+        rr += d * d;
+        bb += b[k] * b[k];
+    }
+    free(Ax);
+    if (bb == 0.0) return sqrt(rr);
+    return sqrt(rr / bb);
+}
+
+/*
+ * Textbook CG: x0 = 0, r = b, p = r; loop Ap = A p, alpha = |r|^2/<p,Ap>,
+ * x += alpha p, r -= alpha Ap, beta = |r_new|^2/|r_old|^2, p = r + beta p;
+ * stop when |r|/|b| <= tol.  Returns 0 when the recomputed true residual is
+ * <= tol, 1 when maxiter was reached first, -5 on <p,Ap> <= 0.
+ */
+int orc_cg(const int L[4], int antiperiodic, const double *U, double mass, const double *b,
+           double *x, double tol, int maxiter, int *iters_out, double *true_res_out)
+{
+    long n = 6 * (volume(L) / 2);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *Ap = (double *)malloc(sizeof(double) * n);
+    int status = 1, it = 0;
+    for (long k = 0; k < n; ++k) { x[k] = 0.0; r[k] = b[k]; p[k] = b[k]; }
+    double bnorm = sqrt(re_dot(n, b, b));
+    double rr = bnorm * bnorm;
+    if (bnorm == 0.0) {
+        status = 0;
+    } else {
+        while (it < maxiter) {
+            orc_mdagm(L, antiperiodic, U, mass, p, Ap);
+            double pAp = re_dot(n, p, Ap);
+            if (!(pAp > 0.0)) { status = -5; break; }
+            double alpha = rr / pAp;
+            for (long k = 0; k < n; ++k) { x[k] += alpha * p[k]; r[k] -= alpha * Ap[k]; }
+            double rr_new = re_dot(n, r, r);
+            ++it;
+            if (sqrt(rr_new) / bnorm <= tol) { status = 0; break; }
+            double beta = rr_new / rr;
+            for (long k = 0; k < n; ++k) p[k] = r[k] + beta * p[k];
+            rr = rr_new;
+        }
+    }
+    double tr = orc_true_residual(L, antiperiodic, U, mass, b, x);
+    if (status == 0 && tr > tol) status = 1;
+    if (iters_out) *iters_out = it;
+    if (true_res_out) *true_res_out = tr;
+    free(r); free(p); free(Ap);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* reduced-precision storage (test reference for quantised inputs)      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Round v to the nearest value of a binary floating-point format with
+ * `mant_bits` stored fraction bits and minimum normal exponent `emin`
+ * (subnormal spacing below it), ties to even.  IEEE binary16: (10, -14);
+ * bfloat16: (7, -126).  Only used on |v| well inside the format's range.
+ * The grid spacing at v is 2^(max(floor(log2|v|), emin) - mant_bits); v is
+ * divided by a power of two (exact) and rounded with rint(), which rounds
+ * half-way cases to even in the default rounding mode.
+ */
+double orc_round_format(double v, int mant_bits, int emin)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    frexp(fabs(v), &e); /* |v| = f 2^e, f in [0.5, 1) -> floor(log2|v|) = e - 1 */
+    int E = e - 1;
+    if (E < emin) E = emin;
+    double spacing = ldexp(1.0, E - mant_bits);
+    return rint(v / spacing) * spacing;
+}
+
+/* format parameters: prec 1 = FP32 (no second rounding), 2 = FP16, 3 = BF16 */
+static void format_of(int prec, int *mant, int *emin)
+{
+    if (prec == 2) { *mant = 10; *emin = -14; }
+    else { *mant = 7; *emin = -126; }
+}
+
+/*
+ * Value a vector site holds after reduced-precision storage, per site of 6 reals:
+ *   prec 1 (FP32): v -> (float)v.
+ *   prec 2/3 (FP16/BF16 with a per-site scale): vf = (float)v; s = max_i |vf_i|
+ *   (FP32); stored code q_i = round_format(vf_i / s) with the quotient taken in
+ *   FP32 (IEEE, correctly rounded); dequantised value = (float)q_i * s in FP32.
+ *   A site with s = 0 stores zeros.
+ */
+void orc_quantize_vectors(int prec, long nsites, const double *in, double *out)
+{
+    for (long i = 0; i < nsites; ++i) {
+        float vf[6];
+        for (int k = 0; k < 6; ++k) vf[k] = (float)in[i * 6 + k];
+        if (prec == 1) {
+            for (int k = 0; k < 6; ++k) out[i * 6 + k] = (double)vf[k];
+            continue;
+        }
+        int mant, emin;
+        format_of(prec, &mant, &emin);
+        float s = 0.0f;
+        for (int k = 0; k < 6; ++k) {
+            float a = fabsf(vf[k]);
+            if (a > s) s = a;
+        }
+        for (int k = 0; k < 6; ++k) {
+            if (s == 0.0f) { out[i * 6 + k] = 0.0; continue; }
+            float quot = vf[k] / s;
+            float q = (float)orc_round_format((double)quot, mant, emin);
+            float deq = q * s;
+            out[i * 6 + k] = (double)deq;
+        }
+    }
+}
+
+/* Value a link element holds after storage: (float)u, then (prec 2/3) rounded
+ * to FP16/BF16 without scaling (|U_ij| <= 1 for SU(3)). */
+void orc_round_links(int prec, long nreals, const double *in, double *out)
+{
+    for (long k = 0; k < nreals; ++k) {
+        float f = (float)in[k];
+        if (prec == 1) { out[k] = (double)f; continue; }
+        int mant, emin;
+        format_of(prec, &mant, &emin);
+        out[k] = orc_round_format((double)f, mant, emin);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* fermion force of S = phi^dagger A^{-1} phi                          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Given X = A^{-1} phi on even sites, with Y = D_oe X on odd sites,
+ *   dS = X^dag dD_eo Y - Y^dag dD_oe X = Psi1^dag dD Psi2,
+ * Psi1 = (X on even, -Y on odd), Psi2 = (X on even, Y on odd).
+ * For the link U = U_mu(x) with s = eta_mu(x) b_mu(x) the variation of D has
+ * s dU at (x, x+mu) and -s dU^dagger at (x+mu, x), so dS = Re Tr(K dU) with
+ *   K_mu(x) = s [ Psi2(x+mu) Psi1(x)^dag - Psi1(x+mu) Psi2(x)^dag ].
+ * Output K as [4][V][3][3] complex.  (The torch-convention gradient
+ * dS/dRe U + i dS/dIm U equals K^dagger.)
+ */
+void orc_force_K(const int L[4], int antiperiodic, const double *U, const double *X_even,
+                 double *Kd)
+{
+    long V = volume(L), Ve = V / 2;
+    cplx *K = (cplx *)Kd;
+    double *Y = (double *)malloc(sizeof(double) * 6 * Ve);
+    double *psi1 = (double *)malloc(sizeof(double) * 6 * V);
+    double *psi2 = (double *)malloc(sizeof(double) * 6 * V);
+    double *tmp = (double *)malloc(sizeof(double) * 6 * V);
+    orc_dslash_oe(L, antiperiodic, U, X_even, Y);
+    /* Psi2 = (X, Y); Psi1 = (X, -Y) */
+    orc_scatter_parity(L, 0, X_even, psi1);
+    orc_scatter_parity(L, 1, Y, tmp);
+    for (long k = 0; k < 6 * V; ++k) {
+        psi2[k] = psi1[k] + tmp[k];
+        psi1[k] = psi1[k] - tmp[k];
+    }
+    const cplx *P1 = (const cplx *)psi1, *P2 = (const cplx *)psi2;
+    for (int mu = 0; mu < 4; ++mu) {
+        for (long i = 0; i < V; ++i) {
+            int x[4], xf[4];
+            coords_of(L, i, x);
+            for (int d = 0; d < 4; ++d) xf[d] = x[d];
+            xf[mu] = (x[mu] + 1) % L[mu];
+            long j = lex_of(L, xf);
+            double s = (double)(eta(mu, x) * bsign(mu, x, L, antiperiodic));
+            cplx *k = K + ((long)mu * V + i) * 9;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    cplx t1 = c_mul(P2[j * 3 + a], c_conj(P1[i * 3 + b]));
+                    cplx t2 = c_mul(P1[j * 3 + a], c_conj(P2[i * 3 + b]));
+                    k[a * 3 + b] = c_scale(s, c_sub(t1, t2));
+                }
+        }
+    }
+    free(Y); free(psi1); free(psi2); free(tmp);
+}
+
+/*
+ * Lie-algebra projection of the force for the left variation
+ * U -> exp(i w T_a) U, T_a = lambda_a / 2 (Gell-Mann):
+ *   f_a = dS/dw_a = Re Tr(i T_a U K),  a = 1..8, stored [4][V][8].
+ */
+void orc_force_lie(long nlinks, const double *Ud, const double *Kd, double *f)
+{
+    const cplx *U = (const cplx *)Ud, *K = (const cplx *)Kd;
+    /* Gell-Mann matrices, entries (re, im), row-major */
+    static const double lam[8][9][2] = {
+        {{0,0},{1,0},{0,0},{1,0},{0,0},{0,0},{0,0},{0,0},{0,0}},
+        {{0,0},{0,-1},{0,0},{0,1},{0,0},{0,0},{0,0},{0,0},{0,0}},
+        {{1,0},{0,0},{0,0},{0,0},{-1,0},{0,0},{0,0},{0,0},{0,0}},
+        {{0,0},{0,0},{1,0},{0,0},{0,0},{0,0},{1,0},{0,0},{0,0}},
+        {{0,0},{0,0},{0,-1},{0,0},{0,0},{0,0},{0,1},{0,0},{0,0}},
+        {{0,0},{0,0},{0,0},{0,0},{0,0},{1,0},{0,0},{1,0},{0,0}},
+        {{0,0},{0,0},{0,0},{0,0},{0,0},{0,-1},{0,0},{0,1},{0,0}},
+        {{0,0},{0,0},{0,0},{0,0},{0,0},{0,0},{0,0},{0,0},{0,0}},
+    };
+    double l8[9][2] = {{0}};
+    double c8 = 1.0 / sqrt(3.0);
+    l8[0][0] = c8; l8[4][0] = c8; l8[8][0] = -2.0 * c8;
+    for (long n = 0; n < nlinks; ++n) {
+        const cplx *u = U + n * 9, *k = K + n * 9;
+        cplx UK[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                cplx s = {0, 0};
+                for (int c = 0; c < 3; ++c) s = c_add(s, c_mul(u[a * 3 + c], k[c * 3 + b]));
+                UK[a * 3 + b] = s;
+            }
+        for (int g = 0; g < 8; ++g) {
+            const double (*lm)[2] = (g == 7) ? (const double (*)[2])l8 : lam[g];
+            /* Tr(i T UK) = (i/2) sum_{ab} lam_ab (UK)_ba */
+            cplx tr = {0, 0};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    cplx la = {lm[a * 3 + b][0], lm[a * 3 + b][1]};
+                    tr = c_add(tr, c_mul(la, UK[b * 3 + a]));
+                }
+            /* Re( i/2 * tr ) = -Im(tr) / 2 */
+            f[n * 8 + g] = -0.5 * tr.im;
+        }
+    }
+}
