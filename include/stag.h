@@ -1,0 +1,162 @@
+/*
+ * stag.h -- C ABI of libstag: even-odd preconditioned staggered operator and
+ * mixed-precision conjugate gradient on one GB300 (sm_103a).
+ *
+ * Method.  Sec. 3 of the paper ("CG Performance") runs a mixed-precision
+ * conjugate-gradient inverter for HYP-smeared staggered quarks on 20^3 x 64
+ * lattices, single precision dominant with a double-precision part.  The paper
+ * does not write the operator; this library implements the standard one-link
+ * staggered operator with these conventions:
+ *
+ *   dims = {Lx, Ly, Lz, Lt}, all even and >= 2; V = Lx Ly Lz Lt, Ve = V / 2;
+ *   lexicographic site index lex = x + Lx (y + Ly (z + Lz t));
+ *   parity (x+y+z+t) mod 2, even = 0; checkerboard index of a site = lex / 2;
+ *   eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}), mu = 0..3 = x, y, z, t;
+ *   b_mu(x) = -1 for mu = t, x_t = Lt - 1 when STAG_ANTIPERIODIC_T is set;
+ *   (D psi)(x) = sum_mu [ eta_mu(x) b_mu(x) U_mu(x) psi(x+mu)
+ *                       - eta_mu(x) b_mu(x-mu) U_mu(x-mu)^dag psi(x-mu) ];
+ *   D_oe: even -> odd sites, D_eo: odd -> even sites;
+ *   A = M^dag M on even sites = 4 m^2 - D_eo D_oe (Hermitian positive definite).
+ *
+ * Data layouts at the ABI (FP64, complex numbers as interleaved (re, im)):
+ *   links:  [4][Lt][Lz][Ly][Lx][3][3][2]  (direction, site, row, column, re/im)
+ *   vector: [Ve][3][2] over the checkerboard index of one parity.
+ * Every pointer argument may be host memory (pageable or pinned) or device
+ * memory of the context's GPU; the library finds out with
+ * cudaPointerGetAttributes and copies host data itself.  The caller owns all
+ * memory it passes; the library never keeps a caller pointer past the call.
+ *
+ * Errors.  Every function returns a status (STAG_OK = 0, STAG_NOT_CONVERGED =
+ * 1, negative = error) and never throws.  stag_last_error() gives a message.
+ * Work is ordered on the context's CUDA stream; each call returns after its
+ * results are in the caller's buffers.  A context is not thread-safe.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAG_ABI_VERSION 1
+
+/* status codes */
+#define STAG_OK 0
+#define STAG_NOT_CONVERGED 1 /* x = last iterate, true_res filled */
+#define STAG_ERR_ARG (-1)    /* bad dims, NULL pointer, bad count/tolerance/precision */
+#define STAG_ERR_CUDA (-2)   /* a CUDA runtime call failed */
+#define STAG_ERR_OOM (-3)    /* device allocation failed */
+#define STAG_ERR_NOT_SU3 (-4) /* reconstruct-12 requested on links that are not SU(3) */
+#define STAG_ERR_BREAKDOWN (-5) /* <p, A p> <= 0 or a non-finite residual in CG */
+#define STAG_ERR_STATE (-7)  /* operator used before stag_links_upload */
+
+/* arithmetic/storage precision of the inner (Krylov) iteration */
+#define STAG_FP64 0 /* FP64 storage and arithmetic */
+#define STAG_FP32 1 /* FP32 storage and arithmetic */
+#define STAG_FP16 2 /* FP16 storage (per-site scale for vectors), FP32 arithmetic */
+#define STAG_BF16 3 /* BF16 storage (per-site scale for vectors), FP32 arithmetic */
+
+/* OR-ed into the precision of stag_dslash_oe/eo and stag_mdagm: hold every
+ * vector at the storage precision and round the output to it, exactly as the
+ * solver's inner iteration does (FP16/BF16: per-site scaled). */
+#define STAG_ROUND_OUTPUT 0x100
+
+/* context flags */
+#define STAG_ANTIPERIODIC_T 1 /* antiperiodic boundary in t (the sign b_mu above) */
+#define STAG_RECON12 2 /* reduced-precision links keep rows 0,1; row 2 = conj(row0 x row1) */
+
+typedef struct stag_ctx stag_ctx;
+
+/*
+ * Create a context for one lattice on the current CUDA device.
+ *   dims[4]     {Lx, Ly, Lz, Lt}: each even and >= 2, V/2 < 2^31.
+ *   flags       STAG_ANTIPERIODIC_T | STAG_RECON12.
+ *   cuda_stream cudaStream_t to order all work on (NULL = legacy default stream).
+ *   out         receives the context.
+ * Errors: STAG_ERR_ARG (dims, out == NULL), STAG_ERR_CUDA, STAG_ERR_OOM.
+ */
+int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out);
+
+/* Free every device buffer of the context.  NULL is accepted. */
+int stag_destroy(stag_ctx *ctx);
+
+/*
+ * Copy a gauge field into the context's own device layouts (Sec. 3: the
+ * operator's one-link smeared SU(3) field).  `links` is [4][V][3][3][2] FP64,
+ * host or device.  The FP64 copy is always kept (true residual, FP64 solves);
+ * FP32/FP16/BF16 copies are made on first use.  Staggered phases and the
+ * boundary sign are applied inside the kernels, never folded into the links.
+ * With STAG_RECON12 the links must be SU(3): a unitarity or determinant
+ * defect above 1e-12 returns STAG_ERR_NOT_SU3.
+ */
+int stag_links_upload(stag_ctx *ctx, const double *links);
+
+/*
+ * out_odd = D_oe in_even (the even -> odd half of the operator).
+ * `precision` selects the storage/arithmetic of the computation: the FP64
+ * input is rounded to it (FP16/BF16: per-site scaled vector, unscaled links),
+ * the operator applied, and the result returned in FP64 without further
+ * rounding (with STAG_ROUND_OUTPUT: rounded to the storage precision, as the
+ * solver stores it).  in_even and out_odd are [Ve][3][2] FP64, host or device, and must
+ * not overlap.  Errors: STAG_ERR_ARG, STAG_ERR_STATE, STAG_ERR_CUDA.
+ */
+int stag_dslash_oe(stag_ctx *ctx, int precision, const double *in_even, double *out_odd);
+
+/* out_even = D_eo in_odd; as stag_dslash_oe with the parities exchanged. */
+int stag_dslash_eo(stag_ctx *ctx, int precision, const double *in_odd, double *out_even);
+
+/*
+ * out_even = (4 m^2 - D_eo D_oe) in_even, the even-site normal operator M^dag M
+ * that the CG of Sec. 3 inverts.  Same conventions as stag_dslash_oe.
+ */
+int stag_mdagm(stag_ctx *ctx, int precision, double mass, const double *in_even,
+               double *out_even);
+
+/*
+ * Solve (4 m^2 - D_eo D_oe) x = b for every source in src[] and every mass in
+ * masses[] (Sec. 3: the mixed-precision CG inverter).  nrhs * nmass systems;
+ * system (r, k) has source src[r], mass masses[k] and solution x[r * nmass + k].
+ *   precision  STAG_FP64: plain FP64 CG.  STAG_FP32/FP16/BF16: the inner
+ *              iteration runs at that storage precision (FP32 arithmetic), the
+ *              solution is accumulated and the residual recomputed in FP64
+ *              whenever the iterated residual has dropped by 10x since the last
+ *              recomputation ("reliable update"), and at convergence.
+ *   tol        stop when ||b - A x|| / ||b|| <= tol, with the residual
+ *              recomputed in FP64 on the GPU (tol > 0).
+ *   maxiter    iteration cap per system (>= 1).
+ *   iters[]    (may be NULL) iterations taken per system.
+ *   true_res[] (may be NULL) final ||b - A x|| / ||b|| recomputed in FP64.
+ * A zero source gives x = 0, 0 iterations, true_res = 0.
+ * Returns STAG_OK when every system converged, STAG_NOT_CONVERGED when some
+ * system hit maxiter (its x is the last iterate), STAG_ERR_BREAKDOWN on a
+ * non-positive <p, A p> or a non-finite residual, STAG_ERR_ARG / _STATE / _CUDA.
+ */
+int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const double masses[],
+                  int nmass, double tol, int maxiter, int precision, double *const x[],
+                  int iters[], double true_res[]);
+
+/*
+ * Average device time of one launch of the solver's half-operator kernel
+ * D_oe at `precision` (the dominant kernel of the CG iteration), measured with
+ * CUDA events around `nlaunch` back-to-back launches on the context stream,
+ * on the context's own internal vectors with the CG's launch configuration.
+ * `bytes_per_launch` (may be NULL) receives the kernel's algorithmic bytes
+ * per launch: 8 links + 1 input vector + 1 output vector per output site.
+ */
+int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_launch,
+                     double *bytes_per_launch);
+
+/* Message of the last error on this context ("" when none). */
+const char *stag_last_error(const stag_ctx *ctx);
+
+/* Static name of a status code. */
+const char *stag_status_string(int status);
+
+/* STAG_ABI_VERSION of the loaded library. */
+int stag_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAG_H */

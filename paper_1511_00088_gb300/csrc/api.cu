@@ -1,0 +1,804 @@
+// api.cu -- libstag's C ABI: context, gauge-field upload, the operator calls
+// and the mixed-precision CG driver (Sec. 3 of the paper: a mixed-precision
+// CG inverter for staggered quarks, single precision dominant, with a double
+// precision part).
+//
+// CG driver.  Per iteration, for every running system j (all on the GPU, no
+// host round trip):
+//   K1  t   = D_oe p                                  (inner precision)
+//   K2  Ap  = 4 m_j^2 p - D_eo t,  <p, Ap>  -> alpha  (FP64 reduction)
+//   K3  r  -= alpha Ap,  x_lo += alpha p,  ||r||^2    (FP64 reduction)
+//       ||r|| < delta * r_max or ||r|| <= tol ||b|| -> reliable update due
+//   if an update is due (a conditional graph node):
+//   K4  x64 += x_lo,  x_lo = 0
+//   K5  t64 = D_oe x64                                (FP64)
+//   K6  r = b - (4 m^2 x64 - D_eo t64) in FP64, stored at the residual's
+//       precision; ||r||^2 in FP64 -> true residual, convergence, beta
+//   K7  p = r + beta p
+// The iteration sits in the body of a CUDA-graph WHILE node whose condition
+// the last block of K3 / K6 sets ("any system still running"); the update
+// kernels sit in an IF node set by K3.  One graph launch runs the whole solve.
+// Without conditional-node support the same kernels run eagerly, with the
+// host polling a device flag every few iterations.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "stag.h"
+
+using namespace stag;
+
+namespace {
+
+size_t cplx_bytes(int P) { return P == P64 ? 16 : P == P32 ? 8 : 4; }
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    reset();
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    n = bytes;
+    return cudaSuccess;
+  }
+};
+
+// a set of nsys checkerboard vectors at one storage precision
+struct VecBuf {
+  DevBuf data, scale;
+  int prec = -1, nsys = 0, Ve = 0;
+  cudaError_t ensure(int P, int ns, int ve) {
+    cudaError_t e = data.ensure(cplx_bytes(P) * 3ull * ns * ve);
+    if (e != cudaSuccess) return e;
+    if (P == P16 || P == PBF) {
+      e = scale.ensure(sizeof(float) * (size_t)ns * ve);
+      if (e != cudaSuccess) return e;
+    }
+    prec = P;
+    nsys = ns;
+    Ve = ve;
+    return cudaSuccess;
+  }
+  VecArg arg() const {
+    VecArg a;
+    a.v = data.p;
+    a.scale = (float *)scale.p;
+    a.sstr = 3ll * Ve;
+    return a;
+  }
+};
+
+struct PinnedBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf &) = delete;
+  PinnedBuf &operator=(const PinnedBuf &) = delete;
+  ~PinnedBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMallocHost(&p, bytes ? bytes : 16);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+};
+
+// solver workspace for one (number of systems, precision, link format)
+struct Work {
+  int nsys = 0, prec = -1, recon = -1;
+  int RP = P32;
+  int NS = 1, G = 1, NS64 = 1, G64 = 1;
+  int nbx_ds = 0, nbx_bl = 0, pstride = 0;
+  VecBuf b64, x64, t64, r, x, p, Ap, t;
+  DevBuf st, partials, tickets, flags;
+  PinnedBuf h_st, h_flags;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+  cudaGraphConditionalHandle h_loop = 0, h_update = 0;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    graph_tried = false;
+  }
+  ~Work() { drop_graph(); }
+};
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct stag_ctx {
+  int dims[4];
+  int flags;
+  int device;
+  cudaStream_t stream;
+  cudaStream_t cap = nullptr, cap2 = nullptr;  // private streams used only for graph capture
+  Geom g;
+  long long V;
+  int Ve;
+  std::string err;
+  bool have_links = false;
+  bool use_graph = true;
+  DevBuf links_canon;  // [4][V][3][3] FP64, kept for lazy reduced-precision copies
+  DevBuf links64;
+  DevBuf links_lo[4][2];
+  bool lo_ok[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
+  DevBuf stage_in, stage_out;  // FP64 ABI-layout vectors for host transfers
+  VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
+  DevBuf defect;
+  Work w;
+};
+
+namespace {
+
+int fail(stag_ctx *c, int code, const char *what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  c->err = buf;
+  cudaGetLastError();
+  return code;
+}
+
+int arg_err(stag_ctx *c, const char *msg) {
+  if (c) c->err = msg;
+  return STAG_ERR_ARG;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? STAG_ERR_OOM : STAG_ERR_CUDA, #call, e_); \
+  } while (0)
+
+#define CKS(expr)            \
+  do {                       \
+    int s_ = (expr);         \
+    if (s_ != STAG_OK) return s_; \
+  } while (0)
+
+int valid_prec(int p) { return p == P64 || p == P32 || p == P16 || p == PBF; }
+
+// device pointer to the FP64 ABI vector `src` (copied through `stage` when on the host)
+int vec_in(stag_ctx *c, const double *src, DevBuf &stage, size_t off_bytes, const double2 **out) {
+  const size_t bytes = sizeof(double) * 6ull * c->Ve;
+  if (is_device_ptr(src)) {
+    *out = reinterpret_cast<const double2 *>(src);
+    return STAG_OK;
+  }
+  CK(stage.ensure(off_bytes + bytes));
+  CK(cudaMemcpyAsync((char *)stage.p + off_bytes, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  *out = reinterpret_cast<const double2 *>((char *)stage.p + off_bytes);
+  return STAG_OK;
+}
+
+// write internal vector k of `v` (precision v.prec) to the FP64 ABI buffer dst
+int vec_out(stag_ctx *c, const VecBuf &v, int k, double *dst) {
+  const size_t bytes = sizeof(double) * 6ull * c->Ve;
+  if (is_device_ptr(dst)) {
+    CK(launch_unpack_vec(v.prec, v.arg(), k, reinterpret_cast<double2 *>(dst), c->Ve, c->stream));
+    return STAG_OK;
+  }
+  CK(c->stage_out.ensure(bytes));
+  CK(launch_unpack_vec(v.prec, v.arg(), k, reinterpret_cast<double2 *>(c->stage_out.p), c->Ve, c->stream));
+  CK(cudaMemcpyAsync(dst, c->stage_out.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return STAG_OK;
+}
+
+int links_for(stag_ctx *c, int P, const void **out) {
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  if (P == P64) {
+    *out = c->links64.p;
+    return STAG_OK;
+  }
+  const int rc = (c->flags & STAG_RECON12) ? 1 : 0;
+  if (!c->lo_ok[P][rc]) {
+    const size_t ne = rc ? 6 : 9;
+    CK(c->links_lo[P][rc].ensure(cplx_bytes(P) * ne * 8ull * c->Ve));
+    CK(launch_pack_links(P, rc, reinterpret_cast<const double2 *>(c->links_canon.p), c->links_lo[P][rc].p,
+                         c->g, c->stream));
+    c->lo_ok[P][rc] = true;
+  }
+  *out = c->links_lo[P][rc].p;
+  return STAG_OK;
+}
+
+int link_recon(const stag_ctx *c, int P) { return (P != P64 && (c->flags & STAG_RECON12)) ? 1 : 0; }
+
+Ctl no_ctl() {
+  Ctl k;
+  memset(&k, 0, sizeof k);
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+
+int work_prepare(stag_ctx *c, int nsys, int prec) {
+  Work &w = c->w;
+  const int recon = link_recon(c, prec);
+  if (w.nsys == nsys && w.prec == prec && w.recon == recon) return STAG_OK;
+  w.drop_graph();
+  w.nsys = nsys;
+  w.prec = prec;
+  w.recon = recon;
+  w.RP = (prec == P64) ? P64 : P32;
+  if (prec == P64) w.NS = nsys >= 4 ? 4 : 1;
+  else w.NS = nsys >= 8 ? 8 : nsys >= 4 ? 4 : 1;
+  w.G = (nsys + w.NS - 1) / w.NS;
+  w.NS64 = nsys >= 4 ? 4 : 1;
+  w.G64 = (nsys + w.NS64 - 1) / w.NS64;
+  const int Ve = c->Ve;
+  w.nbx_ds = (Ve + DS_BT - 1) / DS_BT;
+  w.nbx_bl = (Ve + BLAS_BT - 1) / BLAS_BT;
+  w.pstride = w.nbx_ds > w.nbx_bl ? w.nbx_ds : w.nbx_bl;
+  CK(w.b64.ensure(P64, nsys, Ve));
+  CK(w.x64.ensure(P64, nsys, Ve));
+  CK(w.t64.ensure(P64, nsys, Ve));
+  CK(w.r.ensure(w.RP, nsys, Ve));
+  CK(w.x.ensure(w.RP, nsys, Ve));
+  CK(w.p.ensure(prec, nsys, Ve));
+  CK(w.Ap.ensure(prec, nsys, Ve));
+  CK(w.t.ensure(prec, nsys, Ve));
+  CK(w.st.ensure(sizeof(SysState) * nsys));
+  CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
+  CK(w.tickets.ensure(sizeof(unsigned) * (nsys + 1)));
+  CK(w.flags.ensure(sizeof(int) * 2));
+  CK(w.h_st.ensure(sizeof(SysState) * nsys));
+  CK(w.h_flags.ensure(sizeof(int) * 2));
+  CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * (nsys + 1), c->stream));
+  CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
+  // defined contents for the timing entry point before any solve
+  CK(cudaMemsetAsync(w.p.data.p, 0, w.p.data.n, c->stream));
+  if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
+  return STAG_OK;
+}
+
+Ctl work_ctl(stag_ctx *c, bool graph) {
+  Work &w = c->w;
+  Ctl k;
+  memset(&k, 0, sizeof k);
+  k.st = (SysState *)w.st.p;
+  k.partials = (double *)w.partials.p;
+  k.grp_ticket = (unsigned *)w.tickets.p;
+  k.all_ticket = (unsigned *)w.tickets.p + w.nsys;
+  k.flags = (int *)w.flags.p;
+  k.pstride = w.pstride;
+  k.use_graph_cond = graph ? 1 : 0;
+  k.h_loop = w.h_loop;
+  k.h_update = w.h_update;
+  return k;
+}
+
+DsArgs ds_base(stag_ctx *c) {
+  DsArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = c->g;
+  return a;
+}
+
+BlasArgs blas_base(stag_ctx *c, const Ctl &ctl) {
+  Work &w = c->w;
+  BlasArgs b;
+  memset(&b, 0, sizeof b);
+  b.Ve = c->Ve;
+  b.p = w.p.arg();
+  b.Ap = w.Ap.arg();
+  b.r = w.r.arg();
+  b.x = w.x.arg();
+  b.b = w.b64.arg();
+  b.x64 = w.x64.arg();
+  b.nsys = w.nsys;
+  b.ngroups = w.G;
+  b.ctl = ctl;
+  return b;
+}
+
+// K1..K3
+int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
+  Work &w = c->w;
+  const void *lo = nullptr;
+  CKS(links_for(c, w.prec, &lo));
+  DsArgs a = ds_base(c);
+  a.links = lo;
+  a.nsys = w.nsys;
+  a.ngroups = w.G;
+  a.ctl = ctl;
+  a.gate = GATE_RUNNING;
+  // K1: t = D_oe p
+  a.par_out = 1;
+  a.in = w.p.arg();
+  a.out = w.t.arg();
+  a.fin = FIN_NONE;
+  CK(launch_dslash(w.prec, w.recon, w.prec, w.prec, w.NS, EPI_PLAIN, w.nbx_ds * w.G, s, a));
+  // K2: Ap = 4 m^2 p - D_eo t, <p, Ap>
+  a.par_out = 0;
+  a.in = w.t.arg();
+  a.center = w.p.arg();
+  a.out = w.Ap.arg();
+  a.fin = FIN_ALPHA;
+  CK(launch_dslash(w.prec, w.recon, w.prec, w.prec, w.NS, EPI_MDAGM_DOT, w.nbx_ds * w.G, s, a));
+  // K3: r -= alpha Ap, x += alpha p, ||r||^2
+  BlasArgs b = blas_base(c, ctl);
+  b.gate = GATE_RUNNING;
+  b.fin = FIN_NORM;
+  CK(launch_axpy_norm(w.prec, w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  return STAG_OK;
+}
+
+// K4..K6 (the reliable update; every kernel gated per system)
+int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
+  Work &w = c->w;
+  BlasArgs b = blas_base(c, ctl);
+  b.gate = GATE_UPDATE;
+  b.fin = FIN_NONE;
+  CK(launch_accum_x(w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  DsArgs a = ds_base(c);
+  a.links = c->links64.p;
+  a.nsys = w.nsys;
+  a.ngroups = w.G64;
+  a.ctl = ctl;
+  a.gate = GATE_UPDATE;
+  a.par_out = 1;
+  a.in = w.x64.arg();
+  a.out = w.t64.arg();
+  a.fin = FIN_NONE;
+  CK(launch_dslash(P64, 0, P64, P64, w.NS64, EPI_PLAIN, w.nbx_ds * w.G64, s, a));
+  a.par_out = 0;
+  a.in = w.t64.arg();
+  a.center = w.x64.arg();
+  a.aux = w.b64.arg();
+  a.out = w.r.arg();
+  a.fin = FIN_RESID;
+  CK(launch_dslash(P64, 0, P64, w.RP, w.NS64, EPI_RESID, w.nbx_ds * w.G64, s, a));
+  return STAG_OK;
+}
+
+// K7
+int enqueue_xpay(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
+  Work &w = c->w;
+  BlasArgs b = blas_base(c, ctl);
+  b.gate = GATE_RUNNING;
+  b.fin = FIN_NONE;
+  CK(launch_xpay(w.prec, w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  return STAG_OK;
+}
+
+int build_graph_inner(stag_ctx *c);
+
+// Build the solve graph; on failure close any open capture and report.
+int build_graph(stag_ctx *c) {
+  const int st = build_graph_inner(c);
+  if (st != STAG_OK) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t tmp = nullptr;
+    if (c->cap2 && cudaStreamIsCapturing(c->cap2, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(c->cap2, &tmp);
+    if (c->cap && cudaStreamIsCapturing(c->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(c->cap, &tmp);
+    cudaGetLastError();
+  }
+  return st;
+}
+
+int build_graph_inner(stag_ctx *c) {
+  Work &w = c->w;
+  w.graph_tried = true;
+  if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (!c->cap2) CK(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  w.graph = g;
+  CK(cudaGraphConditionalHandleCreate(&w.h_loop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+  wp.conditional.handle = w.h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  CK(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&w.h_update, body, 0, cudaGraphCondAssignDefault));
+  const Ctl ctl = work_ctl(c, true);
+
+  CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int st = enqueue_main(c, c->cap, ctl);
+  if (st != STAG_OK) {
+    cudaGraph_t tmp;
+    cudaStreamEndCapture(c->cap, &tmp);
+    return st;
+  }
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t capg = nullptr;
+  CK(cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &capg, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+  ip.conditional.handle = w.h_update;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t ifn;
+  CK(cudaGraphAddNode(&ifn, capg, dv.data(), nullptr, dv.size(), &ip));
+  CK(cudaStreamUpdateCaptureDependencies(c->cap, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->cap2, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  st = enqueue_update(c, c->cap2, ctl);
+  {
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(c->cap2, &tmp));
+  }
+  if (st != STAG_OK) return st;
+  st = enqueue_xpay(c, c->cap, ctl);
+  {
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(c->cap, &tmp));
+  }
+  if (st != STAG_OK) return st;
+  CK(cudaGraphInstantiate(&w.exec, g, 0));
+  return STAG_OK;
+}
+
+int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+               double tol, int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
+  const int nsys = nrhs * nmass;
+  CKS(work_prepare(c, nsys, prec));
+  Work &w = c->w;
+  const void *lo = nullptr;
+  CKS(links_for(c, prec, &lo));
+
+  // sources -> b64 (FP64 internal layout)
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *d = nullptr;
+    CKS(vec_in(c, src[r], c->stage_in, 0, &d));
+    for (int k = 0; k < nmass; ++k) CK(launch_pack_vec(P64, d, w.b64.arg(), r * nmass + k, c->Ve, c->stream));
+  }
+  // per-system parameters
+  SysState *hs = (SysState *)w.h_st.p;
+  CK(cudaStreamSynchronize(c->stream));  // pinned staging buffer reuse
+  for (int j = 0; j < nsys; ++j) {
+    memset(&hs[j], 0, sizeof(SysState));
+    const double m = masses[j % nmass];
+    hs[j].m4 = 4.0 * m * m;
+    hs[j].tol = tol;
+    hs[j].delta = (prec == P64) ? 0.0 : 0.1;
+    hs[j].maxiter = maxiter;
+  }
+  CK(cudaMemcpyAsync(w.st.p, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, c->stream));
+  {
+    const Ctl ctl0 = work_ctl(c, false);
+    BlasArgs b = blas_base(c, ctl0);
+    b.gate = GATE_NONE;
+    b.fin = FIN_INIT;
+    CK(launch_cg_init(prec, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
+  }
+
+  bool ran = false;
+  if (c->use_graph) {
+    if (!w.graph_tried) {
+      const int st = build_graph(c);
+      if (st != STAG_OK) {
+        // conditional nodes unavailable: fall back to eager launches
+        w.drop_graph();
+        w.graph_tried = true;
+        c->use_graph = false;
+      }
+    }
+    if (w.exec) {
+      CK(cudaGraphLaunch(w.exec, c->stream));
+      ran = true;
+    }
+  }
+  if (!ran) {
+    const Ctl ctl = work_ctl(c, false);
+    int *hf = (int *)w.h_flags.p;
+    const int chunk = 16;
+    for (long long it = 0; it <= (long long)maxiter + chunk; it += chunk) {
+      for (int i = 0; i < chunk; ++i) {
+        CKS(enqueue_main(c, c->stream, ctl));
+        CKS(enqueue_update(c, c->stream, ctl));
+        CKS(enqueue_xpay(c, c->stream, ctl));
+      }
+      CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if (hf[0] == 0) break;
+    }
+  }
+  CK(cudaMemcpyAsync(hs, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
+  for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
+  CK(cudaStreamSynchronize(c->stream));
+
+  int status = STAG_OK;
+  for (int j = 0; j < nsys; ++j) {
+    if (iters) iters[j] = hs[j].iter;
+    if (true_res) true_res[j] = hs[j].true_res;
+    if (hs[j].done == -5) status = STAG_ERR_BREAKDOWN;
+    else if (hs[j].done != 1 && status == STAG_OK) status = STAG_NOT_CONVERGED;
+  }
+  if (status == STAG_ERR_BREAKDOWN) c->err = "CG breakdown: <p,Ap> <= 0 or non-finite residual";
+  else if (status == STAG_NOT_CONVERGED) c->err = "iteration cap reached before the tolerance";
+  return status;
+}
+
+// operator calls of the ABI: the FP64 input is rounded to `prec` (per-site
+// scaled for FP16/BF16) and the result returned unrounded (FP32 arithmetic),
+// or, with STAG_ROUND_OUTPUT set, rounded to `prec` as inside the solver.
+int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in, double *out) {
+  const bool round_out = (precision & STAG_ROUND_OUTPUT) != 0;
+  const int P = precision & 0xff;
+  if (!valid_prec(P)) return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16");
+  if (!in || !out) return arg_err(c, "NULL vector");
+  const void *links = nullptr;
+  CKS(links_for(c, P, &links));
+  const int recon = link_recon(c, P);
+  const int VP = (P == P64 || P == P32 || round_out) ? P : P32;
+  const int Ve = c->Ve;
+  const double2 *d = nullptr;
+  CKS(vec_in(c, in, c->stage_in, 0, &d));
+  CK(c->api_a.ensure(VP, 1, Ve));
+  CK(c->api_b.ensure(VP, 1, Ve));
+  CK(c->api_c.ensure(VP, 1, Ve));
+  if (VP == P) {
+    CK(launch_pack_vec(P, d, c->api_a.arg(), 0, Ve, c->stream));
+  } else {
+    // round through the storage format, hold the values in FP32
+    CK(c->api_c.ensure(P, 1, Ve));
+    CK(launch_pack_vec(P, d, c->api_c.arg(), 0, Ve, c->stream));
+    CK(launch_convert_vec(P, P32, c->api_c.arg(), c->api_a.arg(), 1, Ve, c->stream));
+  }
+  DsArgs a = ds_base(c);
+  a.links = links;
+  a.nsys = 1;
+  a.ngroups = 1;
+  a.ctl = no_ctl();
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.m4_single = 4.0 * mass * mass;
+  const int nb = (Ve + DS_BT - 1) / DS_BT;
+  if (which == 0 || which == 1) {  // 0: D_oe (out odd), 1: D_eo (out even)
+    a.par_out = which == 0 ? 1 : 0;
+    a.in = c->api_a.arg();
+    a.out = c->api_b.arg();
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, nb, c->stream, a));
+  } else {  // M^dag M
+    a.par_out = 1;
+    a.in = c->api_a.arg();
+    a.out = c->api_c.arg();
+    CK(c->api_c.ensure(VP, 1, Ve));
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, nb, c->stream, a));
+    a.par_out = 0;
+    a.in = c->api_c.arg();
+    a.center = c->api_a.arg();
+    a.out = c->api_b.arg();
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_MDAGM, nb, c->stream, a));
+  }
+  CKS(vec_out(c, c->api_b, 0, out));
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int stag_abi_version(void) { return STAG_ABI_VERSION; }
+
+const char *stag_status_string(int s) {
+  switch (s) {
+    case STAG_OK: return "STAG_OK";
+    case STAG_NOT_CONVERGED: return "STAG_NOT_CONVERGED";
+    case STAG_ERR_ARG: return "STAG_ERR_ARG";
+    case STAG_ERR_CUDA: return "STAG_ERR_CUDA";
+    case STAG_ERR_OOM: return "STAG_ERR_OOM";
+    case STAG_ERR_NOT_SU3: return "STAG_ERR_NOT_SU3";
+    case STAG_ERR_BREAKDOWN: return "STAG_ERR_BREAKDOWN";
+    case STAG_ERR_STATE: return "STAG_ERR_STATE";
+  }
+  return "STAG_UNKNOWN_STATUS";
+}
+
+const char *stag_last_error(const stag_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out) {
+  if (!out || !dims) return STAG_ERR_ARG;
+  *out = nullptr;
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2 || (dims[m] & 1)) return STAG_ERR_ARG;
+    V *= dims[m];
+  }
+  if (V / 2 >= (1ll << 31) / 3) return STAG_ERR_ARG;
+  if (flags & ~(STAG_ANTIPERIODIC_T | STAG_RECON12)) return STAG_ERR_ARG;
+  stag_ctx *c = new stag_ctx();
+  for (int m = 0; m < 4; ++m) c->dims[m] = dims[m];
+  c->flags = flags;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->V = V;
+  c->Ve = (int)(V / 2);
+  c->g.L0 = dims[0];
+  c->g.L1 = dims[1];
+  c->g.L2 = dims[2];
+  c->g.L3 = dims[3];
+  c->g.Lxh = dims[0] / 2;
+  c->g.Ve = c->Ve;
+  c->g.ap = (flags & STAG_ANTIPERIODIC_T) ? 1 : 0;
+  const char *eager = getenv("STAG_EAGER");
+  c->use_graph = !(eager && eager[0] == '1');
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return STAG_ERR_CUDA;
+  }
+  *out = c;
+  return STAG_OK;
+}
+
+int stag_destroy(stag_ctx *c) {
+  if (!c) return STAG_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->w.drop_graph();
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
+  delete c;
+  return STAG_OK;
+}
+
+int stag_links_upload(stag_ctx *c, const double *links) {
+  if (!c) return STAG_ERR_ARG;
+  if (!links) return arg_err(c, "NULL links");
+  CK(cudaSetDevice(c->device));
+  const size_t bytes = sizeof(double) * 18ull * 4ull * c->V;
+  CK(c->links_canon.ensure(bytes));
+  CK(cudaMemcpyAsync(c->links_canon.p, links, bytes, cudaMemcpyDefault, c->stream));
+  if (c->flags & STAG_RECON12) {
+    CK(c->defect.ensure(sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(c->defect.p, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_su3_defect(reinterpret_cast<const double2 *>(c->links_canon.p), 4ll * c->V,
+                         (unsigned long long *)c->defect.p, c->stream));
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->defect.p, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    if (!(d <= 1e-12)) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "links are not SU(3) (defect %.3e > 1e-12); reconstruct-12 needs SU(3)", d);
+      c->err = buf;
+      c->have_links = false;
+      return STAG_ERR_NOT_SU3;
+    }
+  }
+  CK(c->links64.ensure(cplx_bytes(P64) * 9ull * 8ull * c->Ve));
+  CK(launch_pack_links(P64, 0, reinterpret_cast<const double2 *>(c->links_canon.p), c->links64.p, c->g,
+                       c->stream));
+  for (int p = 0; p < 4; ++p) c->lo_ok[p][0] = c->lo_ok[p][1] = false;
+  c->have_links = true;
+  c->w.drop_graph();  // the graph holds link pointers of the reduced-precision copies
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
+}
+
+int stag_dslash_oe(stag_ctx *c, int precision, const double *in_even, double *out_odd) {
+  if (!c) return STAG_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  return op_impl(c, 0, precision, 0.0, in_even, out_odd);
+}
+
+int stag_dslash_eo(stag_ctx *c, int precision, const double *in_odd, double *out_even) {
+  if (!c) return STAG_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  return op_impl(c, 1, precision, 0.0, in_odd, out_even);
+}
+
+int stag_mdagm(stag_ctx *c, int precision, double mass, const double *in_even, double *out_even) {
+  if (!c) return STAG_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  return op_impl(c, 2, precision, mass, in_even, out_even);
+}
+
+int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+                  double tol, int maxiter, int precision, double *const x[], int iters[],
+                  double true_res[]) {
+  if (!c) return STAG_ERR_ARG;
+  if (!src || !masses || !x) return arg_err(c, "NULL argument");
+  if (nrhs < 1 || nmass < 1) return arg_err(c, "nrhs and nmass must be >= 1");
+  if ((long long)nrhs * nmass > 4096) return arg_err(c, "at most 4096 systems per solve");
+  if (!(tol > 0.0) || !(tol < 1.0)) return arg_err(c, "tol must be in (0, 1)");
+  if (maxiter < 1) return arg_err(c, "maxiter must be >= 1");
+  if (!valid_prec(precision)) return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16");
+  for (int r = 0; r < nrhs; ++r)
+    if (!src[r]) return arg_err(c, "NULL source");
+  for (int j = 0; j < nrhs * nmass; ++j)
+    if (!x[j]) return arg_err(c, "NULL solution buffer");
+  for (int k = 0; k < nmass; ++k)
+    if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
+  CK(cudaSetDevice(c->device));
+  return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_launch,
+                     double *bytes_per_launch) {
+  if (!c) return STAG_ERR_ARG;
+  if (!valid_prec(precision) || nlaunch < 1 || !ms_per_launch) return arg_err(c, "bad argument");
+  CK(cudaSetDevice(c->device));
+  const int nsys = c->w.nsys > 0 && c->w.prec == precision ? c->w.nsys : 1;
+  CKS(work_prepare(c, nsys, precision));
+  Work &w = c->w;
+  const void *lo = nullptr;
+  CKS(links_for(c, precision, &lo));
+  DsArgs a = ds_base(c);
+  a.links = lo;
+  a.nsys = w.nsys;
+  a.ngroups = w.G;
+  a.ctl = work_ctl(c, false);
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.par_out = 1;
+  a.in = w.p.arg();
+  a.out = w.t.arg();
+  const int nb = w.nbx_ds * w.G;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(launch_dslash(precision, w.recon, precision, precision, w.NS, EPI_PLAIN, nb, c->stream, a));
+  CK(cudaEventRecord(e0, c->stream));
+  for (int i = 0; i < nlaunch; ++i)
+    CK(launch_dslash(precision, w.recon, precision, precision, w.NS, EPI_PLAIN, nb, c->stream, a));
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = (double)ms / nlaunch;
+  if (bytes_per_launch) {
+    const double lb = (double)cplx_bytes(precision) * (w.recon ? 6 : 9);
+    const double vb = (double)cplx_bytes(precision) * 3 + ((precision == P16 || precision == PBF) ? 4 : 0);
+    *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * 2.0 * vb);
+  }
+  return STAG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// blas.cu -- launchers of the fused BLAS-1 kernels, layout conversions, the
+// SU(3) check, and the dispatcher of the half-operator instantiations.
+#include "launch.h"
+
+namespace stag {
+
+cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                          cudaStream_t st, const DsArgs &a) {
+  switch (LP) {
+    case P64: return launch_dslash_p64(recon, VP, OP, NS, EPI, nblocks, st, a);
+    case P32: return launch_dslash_p32(recon, VP, OP, NS, EPI, nblocks, st, a);
+    case P16: return launch_dslash_p16(recon, VP, OP, NS, EPI, nblocks, st, a);
+    case PBF: return launch_dslash_pbf(recon, VP, OP, NS, EPI, nblocks, st, a);
+  }
+  return cudaErrorNotSupported;
+}
+
+// (VP, RP) pairs used by the solver: (P64,P64) FP64 CG; (P32,P32), (P16,P32),
+// (PBF,P32) mixed precision with FP32 residual and iterate.
+#define STAG_BLAS_PAIRS(X, NS_) \
+  X(P64, P64, NS_) X(P32, P32, NS_) X(P16, P32, NS_) X(PBF, P32, NS_)
+
+#define STAG_AXPY(VP_, RP_, NS_)                                               \
+  if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
+    k_axpy_norm<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);       \
+    return cudaGetLastError();                                                 \
+  }
+#define STAG_XPAY(VP_, RP_, NS_)                                               \
+  if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
+    k_xpay<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);            \
+    return cudaGetLastError();                                                 \
+  }
+#define STAG_INIT(VP_, RP_, NS_)                                               \
+  if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
+    k_cg_init<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);         \
+    return cudaGetLastError();                                                 \
+  }
+
+cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
+  STAG_BLAS_PAIRS(STAG_AXPY, 1)
+  STAG_BLAS_PAIRS(STAG_AXPY, 4)
+  STAG_BLAS_PAIRS(STAG_AXPY, 8)
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_xpay(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
+  STAG_BLAS_PAIRS(STAG_XPAY, 1)
+  STAG_BLAS_PAIRS(STAG_XPAY, 4)
+  STAG_BLAS_PAIRS(STAG_XPAY, 8)
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
+  STAG_BLAS_PAIRS(STAG_INIT, 1)
+  STAG_BLAS_PAIRS(STAG_INIT, 4)
+  STAG_BLAS_PAIRS(STAG_INIT, 8)
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
+#define STAG_ACC(RP_, NS_)                                                     \
+  if (RP == RP_ && NS == NS_) {                                                \
+    k_accum_x<RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);              \
+    return cudaGetLastError();                                                 \
+  }
+  STAG_ACC(P64, 1) STAG_ACC(P64, 4) STAG_ACC(P64, 8)
+  STAG_ACC(P32, 1) STAG_ACC(P32, 4) STAG_ACC(P32, 8)
+#undef STAG_ACC
+  return cudaErrorNotSupported;
+}
+
+static inline int nblk(long long n, int bt) { return (int)((n + bt - 1) / bt); }
+
+cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st) {
+  const int nb = nblk(Ve, 256);
+  switch (P) {
+    case P64: k_pack_vec<P64><<<nb, 256, 0, st>>>(src, dst, k, Ve); break;
+    case P32: k_pack_vec<P32><<<nb, 256, 0, st>>>(src, dst, k, Ve); break;
+    case P16: k_pack_vec<P16><<<nb, 256, 0, st>>>(src, dst, k, Ve); break;
+    case PBF: k_pack_vec<PBF><<<nb, 256, 0, st>>>(src, dst, k, Ve); break;
+    default: return cudaErrorNotSupported;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_vec(int P, VecArg src, int k, double2 *dst, int Ve, cudaStream_t st) {
+  const int nb = nblk(Ve, 256);
+  switch (P) {
+    case P64: k_unpack_vec<P64><<<nb, 256, 0, st>>>(src, k, dst, Ve); break;
+    case P32: k_unpack_vec<P32><<<nb, 256, 0, st>>>(src, k, dst, Ve); break;
+    case P16: k_unpack_vec<P16><<<nb, 256, 0, st>>>(src, k, dst, Ve); break;
+    case PBF: k_unpack_vec<PBF><<<nb, 256, 0, st>>>(src, k, dst, Ve); break;
+    default: return cudaErrorNotSupported;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int nsys, int Ve,
+                               cudaStream_t st) {
+  const int nb = nblk((long long)nsys * Ve, 256);
+#define STAG_CV(A, B)                                                          \
+  if (PIN == A && POUT == B) {                                                 \
+    k_convert_vec<A, B><<<nb, 256, 0, st>>>(src, dst, nsys, Ve);               \
+    return cudaGetLastError();                                                 \
+  }
+  STAG_CV(P16, P32) STAG_CV(PBF, P32) STAG_CV(P32, P16) STAG_CV(P32, PBF)
+  STAG_CV(P64, P16) STAG_CV(P64, PBF) STAG_CV(P64, P32)
+#undef STAG_CV
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_pack_links(int LP, int recon, const double2 *src, void *dst, Geom g,
+                              cudaStream_t st) {
+  const long long n = 8ll * g.Ve;  // 4 V links
+  const int nb = nblk(n, 256);
+#define STAG_PL(A, R)                                                          \
+  if (LP == A && recon == R) {                                                 \
+    k_pack_links<A, R><<<nb, 256, 0, st>>>(src, dst, g);                       \
+    return cudaGetLastError();                                                 \
+  }
+  STAG_PL(P64, 0) STAG_PL(P32, 0) STAG_PL(P32, 1) STAG_PL(P16, 0) STAG_PL(P16, 1)
+  STAG_PL(PBF, 0) STAG_PL(PBF, 1)
+#undef STAG_PL
+  return cudaErrorNotSupported;
+}
+
+// max over links of max(|U U^dag - 1|_max, |det U - 1|), FP64
+__global__ void k_su3_defect(const double2 *__restrict__ U, long long nlinks, unsigned long long *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (i < nlinks) {
+    double2 u[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = U[i * 9 + e];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double re = 0.0, im = 0.0;  // (U U^dag)_ab = sum_c U_ac conj(U_bc)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 x = u[3 * a + c], y = u[3 * b + c];
+          re += x.x * y.x + x.y * y.y;
+          im += x.y * y.x - x.x * y.y;
+        }
+        if (a == b) re -= 1.0;
+        d = fmax(d, fmax(fabs(re), fabs(im)));
+      }
+    // det = u0 (u4 u8 - u5 u7) - u1 (u3 u8 - u5 u6) + u2 (u3 u7 - u4 u6)
+    auto mul = [](double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+    auto sub = [](double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); };
+    const double2 c0 = sub(mul(u[4], u[8]), mul(u[5], u[7]));
+    const double2 c1 = sub(mul(u[3], u[8]), mul(u[5], u[6]));
+    const double2 c2 = sub(mul(u[3], u[7]), mul(u[4], u[6]));
+    const double2 t0 = mul(u[0], c0), t1 = mul(u[1], c1), t2 = mul(u[2], c2);
+    const double dre = t0.x - t1.x + t2.x - 1.0, dim = t0.y - t1.y + t2.y;
+    d = fmax(d, fmax(fabs(dre), fabs(dim)));
+    if (!(d == d)) d = 1e300;  // NaN counts as a defect
+  }
+  // block max, then one atomic per block (non-negative doubles order as uint64)
+  __shared__ double sm[256];
+  sm[threadIdx.x] = d;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));
+}
+
+cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
+                              cudaStream_t st) {
+  k_su3_defect<<<nblk(nlinks, 256), 256, 0, st>>>(U, nlinks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stag

@@ -1,0 +1,16 @@
+// dslash_inst.cuh -- instantiation table of the half-operator kernel (one
+// translation unit per link precision, so they compile in parallel).
+#pragma once
+#include "launch.h"
+
+#define STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_)                                      \
+  if (recon == RC_ && VP == VP_ && OP == OP_ && NS == NS_ && EPI == EPI_) {              \
+    k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT><<<nblocks, DS_BT, 0, st>>>(a);         \
+    return cudaGetLastError();                                                           \
+  }
+
+// plain, mass epilogue, mass epilogue + dot
+#define STAG_DS_EPIS(LP_, RC_, VP_, OP_, NS_)                \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN)          \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM)          \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM_DOT)

@@ -1,0 +1,39 @@
+// launch.h -- host-side launchers of libstag's kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stag_kernels.cuh"
+
+namespace stag {
+
+constexpr int DS_BT = 128;    // threads per block of the half-operator kernels
+constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
+
+// Launch k_dslash<LP, recon, VP, OP, NS, EPI> on `nblocks` blocks.  Returns
+// cudaErrorNotSupported for a combination the library does not instantiate.
+cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                          cudaStream_t st, const DsArgs &a);
+cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                              cudaStream_t st, const DsArgs &a);
+cudaError_t launch_dslash_p32(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                              cudaStream_t st, const DsArgs &a);
+cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                              cudaStream_t st, const DsArgs &a);
+cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+                              cudaStream_t st, const DsArgs &a);
+
+cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+cudaError_t launch_xpay(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+
+cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st);
+cudaError_t launch_unpack_vec(int P, VecArg src, int k, double2 *dst, int Ve, cudaStream_t st);
+cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int nsys, int Ve,
+                               cudaStream_t st);
+cudaError_t launch_pack_links(int LP, int recon, const double2 *src, void *dst, Geom g,
+                              cudaStream_t st);
+cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
+                              cudaStream_t st);
+
+}  // namespace stag

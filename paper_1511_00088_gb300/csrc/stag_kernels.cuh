@@ -1,0 +1,786 @@
+// stag_kernels.cuh -- device code of libstag (sm_103a): the staggered half
+// operator D_oe / D_eo with fused epilogues, the fused BLAS-1 steps of CG,
+// deterministic FP64 cross-CTA reductions and the reliable-update bookkeeping.
+//
+// Operator (the one-link staggered operator inside the mixed-precision CG of
+// Sec. 3 of the paper; the paper names it without writing it down):
+//   (D psi)(x) = sum_mu [ eta_mu(x) b_mu(x) U_mu(x) psi(x+mu)
+//                       - eta_mu(x) b_mu(x-mu) U_mu(x-mu)^dag psi(x-mu) ]
+//   eta_mu(x) = (-1)^(x_0+...+x_{mu-1}), b_t = -1 on the link from t = Lt-1
+//   (antiperiodic time), applied from the coordinates, never folded into U.
+//
+// Device layouts (structure of arrays, coalesced in the site index s):
+//   links  [parity][mu][element e][Ve]  complex (e = 3 row + col; 9, or 6 with
+//          reconstruct-12 where row 2 = conj(row0 x row1) is rebuilt in registers)
+//   vector [system][colour][Ve] complex; FP16/BF16 vectors add one FP32 scale
+//          per site and system: value = code * scale, scale = max |component|.
+// One thread owns one output site and NS systems; the 8 links of the site are
+// loaded once into registers and applied to all NS systems.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stag {
+
+enum { P64 = 0, P32 = 1, P16 = 2, PBF = 3 };
+
+template <int P> struct Tr;
+template <> struct Tr<P64> { typedef double R; typedef double2 S2; static constexpr bool scaled = false; };
+template <> struct Tr<P32> { typedef float R; typedef float2 S2; static constexpr bool scaled = false; };
+template <> struct Tr<P16> { typedef float R; typedef __half2 S2; static constexpr bool scaled = true; };
+template <> struct Tr<PBF> { typedef float R; typedef __nv_bfloat162 S2; static constexpr bool scaled = true; };
+
+// ---------------------------------------------------------------------------
+// plain-old-data argument blocks (passed by value to kernels)
+// ---------------------------------------------------------------------------
+struct Geom {
+  int L0, L1, L2, L3;  // Lx, Ly, Lz, Lt
+  int Lxh;             // Lx / 2
+  int Ve;              // sites per parity
+  int ap;              // antiperiodic time boundary
+};
+
+struct VecArg {
+  void *v;          // [nsys][3][Ve] complex of the storage type
+  float *scale;     // [nsys][Ve] (FP16/BF16 only)
+  long long sstr;   // complex elements per system (3 * Ve)
+};
+
+// per-system CG state in device memory (FP64 scalars of the mixed CG)
+struct SysState {
+  double m4;        // 4 m^2
+  double bnorm2;    // ||b||^2
+  double rho;       // ||r||^2 of the iterated residual
+  double pAp;       // <p, A p>
+  double alpha, beta;
+  double rmax;      // ||r|| at the last reliable update (FP64)
+  double true_res;  // ||b - A x|| / ||b|| at the last reliable update
+  double tol;       // stop when ||b - A x|| / ||b|| <= tol
+  double delta;     // reliable update when ||r|| < delta * rmax (0: only at tol)
+  int maxiter;
+  int iter;
+  int done;         // 0 running, 1 converged, 2 iteration cap, -5 breakdown
+  int update;       // a reliable update is due this iteration
+  int n_updates;
+  int pad_;
+};
+
+struct Ctl {
+  SysState *st;          // [nsys]
+  double *partials;      // [nsys][NVMAX][pstride]
+  unsigned *grp_ticket;  // [ngroups]
+  unsigned *all_ticket;  // [1]
+  int *flags;            // [0] any system running, [1] any reliable update due
+  int pstride;           // partial slots per (system, value)
+  int use_graph_cond;    // call cudaGraphSetConditional on the handles below
+  cudaGraphConditionalHandle h_loop, h_update;
+};
+
+enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_UPDATE = 2 };
+enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_MDAGM_DOT = 2, EPI_RESID = 3 };
+enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_NORM = 2, FIN_RESID = 3, FIN_INIT = 4 };
+
+struct DsArgs {
+  Geom g;
+  int par_out;           // parity of the output sites
+  const void *links;     // [2][4][NE][Ve] of the link storage type
+  VecArg in;             // input on the other parity
+  VecArg center;         // EPI_MDAGM*: the vector the mass term multiplies; EPI_RESID: x
+  VecArg out;            // output (EPI_RESID: the reduced-precision residual)
+  VecArg aux;            // EPI_RESID: the source b (FP64)
+  double m4_single;      // 4 m^2 when ctl == nullptr
+  int nsys, ngroups;
+  Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
+  int gate, fin;
+};
+
+struct BlasArgs {
+  int Ve;
+  VecArg p, Ap, r, x, b, x64;   // meanings per kernel
+  int nsys, ngroups;
+  Ctl ctl;
+  int gate, fin;
+};
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 to_r2(double2 a) { return a; }
+__device__ __forceinline__ float2 to_r2(float2 a) { return a; }
+__device__ __forceinline__ float2 to_r2(__half2 a) { return __half22float2(a); }
+__device__ __forceinline__ float2 to_r2(__nv_bfloat162 a) { return __bfloat1622float2(a); }
+
+template <int P> __device__ __forceinline__ typename Tr<P>::S2 from_r(typename Tr<P>::R re, typename Tr<P>::R im);
+template <> __device__ __forceinline__ double2 from_r<P64>(double re, double im) { return make_double2(re, im); }
+template <> __device__ __forceinline__ float2 from_r<P32>(float re, float im) { return make_float2(re, im); }
+template <> __device__ __forceinline__ __half2 from_r<P16>(float re, float im) {
+  return __halves2half2(__float2half_rn(re), __float2half_rn(im));
+}
+template <> __device__ __forceinline__ __nv_bfloat162 from_r<PBF>(float re, float im) {
+  return __halves2bfloat162(__float2bfloat16_rn(re), __float2bfloat16_rn(im));
+}
+
+template <class S2> __device__ __forceinline__ S2 ldg2(const S2 *p) { return __ldg(p); }
+template <> __device__ __forceinline__ __half2 ldg2<__half2>(const __half2 *p) {
+  unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+  return *reinterpret_cast<__half2 *>(&u);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 ldg2<__nv_bfloat162>(const __nv_bfloat162 *p) {
+  unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+  return *reinterpret_cast<__nv_bfloat162 *>(&u);
+}
+
+// ---------------------------------------------------------------------------
+// vectors
+// ---------------------------------------------------------------------------
+template <int P, class R>
+__device__ __forceinline__ void load_vec(const VecArg &f, int k, int s, int Ve, R (&v)[6]) {
+  typedef typename Tr<P>::S2 S2;
+  const S2 *p = reinterpret_cast<const S2 *>(f.v) + (long long)k * f.sstr + s;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    auto w = to_r2(ldg2(p + (long long)c * Ve));
+    v[2 * c] = (R)w.x;
+    v[2 * c + 1] = (R)w.y;
+  }
+  if (Tr<P>::scaled) {
+    const float sc = __ldg(f.scale + (long long)k * Ve + s);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = (R)((float)v[i] * sc);
+  }
+}
+
+// coherent (non-ldg) load, for vectors the same kernel also writes
+template <int P, class R>
+__device__ __forceinline__ void load_vec_rw(const VecArg &f, int k, int s, int Ve, R (&v)[6]) {
+  typedef typename Tr<P>::S2 S2;
+  const S2 *p = reinterpret_cast<const S2 *>(f.v) + (long long)k * f.sstr + s;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    auto w = to_r2(p[(long long)c * Ve]);
+    v[2 * c] = (R)w.x;
+    v[2 * c + 1] = (R)w.y;
+  }
+  if (Tr<P>::scaled) {
+    const float sc = f.scale[(long long)k * Ve + s];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = (R)((float)v[i] * sc);
+  }
+}
+
+// Store one site.  FP16/BF16: scale = max_i |v_i| (FP32), code_i =
+// round-to-nearest-even(v_i / scale) with the quotient correctly rounded in
+// FP32; a zero site stores zero codes and scale 0.
+template <int P, class R>
+__device__ __forceinline__ void store_vec(const VecArg &f, int k, int s, int Ve, const R (&v)[6]) {
+  typedef typename Tr<P>::S2 S2;
+  typedef typename Tr<P>::R SR;
+  S2 *p = reinterpret_cast<S2 *>(f.v) + (long long)k * f.sstr + s;
+  if (Tr<P>::scaled) {
+    float a[6];
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      a[i] = (float)v[i];
+      m = fmaxf(m, fabsf(a[i]));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float qr = 0.f, qi = 0.f;
+      if (m > 0.f) {
+        qr = __fdiv_rn(a[2 * c], m);
+        qi = __fdiv_rn(a[2 * c + 1], m);
+      }
+      p[(long long)c * Ve] = from_r<P>((SR)qr, (SR)qi);
+    }
+    f.scale[(long long)k * Ve + s] = m;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[(long long)c * Ve] = from_r<P>((SR)v[2 * c], (SR)v[2 * c + 1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// links
+// ---------------------------------------------------------------------------
+template <int LP, int RECON, class R>
+__device__ __forceinline__ void load_link(const void *base, int Ve, int par, int mu, int s, R (&u)[18]) {
+  typedef typename Tr<LP>::S2 S2;
+  constexpr int NE = RECON ? 6 : 9;
+  const S2 *p = reinterpret_cast<const S2 *>(base) + (long long)((par * 4 + mu) * NE) * Ve + s;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    auto w = to_r2(ldg2(p + (long long)e * Ve));
+    u[2 * e] = (R)w.x;
+    u[2 * e + 1] = (R)w.y;
+  }
+  if (RECON) {
+    // row2 = conj(row0 x row1): c0 = conj(a1 b2 - a2 b1), c1 = conj(a2 b0 - a0 b2),
+    // c2 = conj(a0 b1 - a1 b0), a = row 0, b = row 1
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int i = (c + 1) % 3, j = (c + 2) % 3;
+      const R ar_i = u[2 * i], ai_i = u[2 * i + 1], ar_j = u[2 * j], ai_j = u[2 * j + 1];
+      const R br_i = u[6 + 2 * i], bi_i = u[6 + 2 * i + 1], br_j = u[6 + 2 * j], bi_j = u[6 + 2 * j + 1];
+      const R re = (ar_i * br_j - ai_i * bi_j) - (ar_j * br_i - ai_j * bi_i);
+      const R im = (ar_i * bi_j + ai_i * br_j) - (ar_j * bi_i + ai_j * br_i);
+      u[12 + 2 * c] = re;
+      u[12 + 2 * c + 1] = -im;
+    }
+  }
+}
+
+// acc += sgn * (U v)
+template <class R>
+__device__ __forceinline__ void mv_acc(const R (&u)[18], const R (&v)[6], R sgn, R (&acc)[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R hr = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R ur = u[2 * (3 * a + b)], ui = u[2 * (3 * a + b) + 1];
+      hr += ur * v[2 * b] - ui * v[2 * b + 1];
+      hi += ur * v[2 * b + 1] + ui * v[2 * b];
+    }
+    acc[2 * a] += sgn * hr;
+    acc[2 * a + 1] += sgn * hi;
+  }
+}
+
+// acc += sgn * (U^dag v)
+template <class R>
+__device__ __forceinline__ void mvdag_acc(const R (&u)[18], const R (&v)[6], R sgn, R (&acc)[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R hr = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R ur = u[2 * (3 * b + a)], ui = u[2 * (3 * b + a) + 1];
+      hr += ur * v[2 * b] + ui * v[2 * b + 1];
+      hi += ur * v[2 * b + 1] - ui * v[2 * b];
+    }
+    acc[2 * a] += sgn * hr;
+    acc[2 * a + 1] += sgn * hi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void site_coords(const Geom &g, int par, int s, int (&x)[4]) {
+  const int xh = s % g.Lxh;
+  int r = s / g.Lxh;
+  x[1] = r % g.L1;
+  r /= g.L1;
+  x[2] = r % g.L2;
+  x[3] = r / g.L2;
+  x[0] = 2 * xh + ((par + x[1] + x[2] + x[3]) & 1);
+}
+
+__device__ __forceinline__ int cb_of(const Geom &g, int x0, int x1, int x2, int x3) {
+  return (x0 >> 1) + g.Lxh * (x1 + g.L1 * (x2 + g.L2 * x3));
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions: per-block partials, the last block of a group sums
+// them in a fixed order and runs the finaliser of each system of the group;
+// the last group to finish publishes the loop/update flags.
+// ---------------------------------------------------------------------------
+constexpr int NVMAX = 2;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys) {
+  if (j >= nsys) return false;
+  if (gate == GATE_NONE || c.st == nullptr) return true;
+  const SysState &s = c.st[j];
+  if (gate == GATE_RUNNING) return s.done == 0;
+  return s.done == 0 && s.update != 0;
+}
+
+__device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, const double *sum) {
+  SysState &s = c.st[j];
+  if (fin == FIN_ALPHA) {
+    const double pAp = sum[0];
+    s.pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      s.done = -5;
+      return;
+    }
+    s.alpha = s.rho / pAp;
+  } else if (fin == FIN_NORM) {
+    const double rr = sum[0];
+    s.iter += 1;
+    if (!isfinite(rr)) {
+      s.done = -5;
+      return;
+    }
+    if (s.iter > s.maxiter + 2) {
+      // hard stop: the forced update at maxiter did not run
+      s.done = 2;
+      return;
+    }
+    const double rn = sqrt(rr);
+    const double bn = sqrt(s.bnorm2);
+    if (rn < s.delta * s.rmax || rn <= s.tol * bn || s.iter >= s.maxiter) {
+      s.update = 1;  // beta and rho are set after the FP64 recomputation
+    } else {
+      s.beta = rr / s.rho;
+      s.rho = rr;
+    }
+  } else if (fin == FIN_RESID) {
+    const double rr = sum[0];
+    s.update = 0;
+    s.n_updates += 1;
+    if (!isfinite(rr)) {
+      s.done = -5;
+      return;
+    }
+    s.true_res = sqrt(rr / s.bnorm2);
+    s.rmax = sqrt(rr);
+    if (s.true_res <= s.tol) {
+      s.done = 1;
+    } else if (s.iter >= s.maxiter) {
+      s.done = 2;
+    } else {
+      s.beta = rr / s.rho;
+      s.rho = rr;
+    }
+  } else if (fin == FIN_INIT) {
+    s.bnorm2 = sum[0];
+    s.rho = sum[1];
+    s.rmax = sqrt(sum[0]);
+    s.iter = 0;
+    s.update = 0;
+    s.n_updates = 0;
+    s.alpha = s.beta = s.pAp = 0.0;
+    if (sum[0] == 0.0) {
+      s.true_res = 0.0;
+      s.done = 1;
+    } else {
+      s.true_res = 1.0;
+      s.done = 0;
+    }
+  }
+}
+
+// Called by every thread of every block after it accumulated val[k][v] for
+// the NS systems j0 + k of its group.  bx/nbx: block index / count within the
+// group.  Deterministic: partials are summed in block order by fixed trees.
+template <int NS, int NV>
+__device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, double (&val)[NS][NV], int grp,
+                                                    int ngroups, int j0, int nsys, int bx, int nbx) {
+  __shared__ double red[32][NS * NV];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double w = warp_sum(val[k][v]);
+      if (lane == 0) red[warp][k * NV + v] = w;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // one thread publishes the block's partials, then takes a ticket
+    for (int kv = 0; kv < NS * NV; ++kv) {
+      const int k = kv / NV, v = kv % NV;
+      double s = 0.0;
+      for (int w = 0; w < nwarp; ++w) s += red[w][kv];
+      if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = s;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(c.grp_ticket + grp, 1u);
+    am_last = (t == (unsigned)(nbx - 1));
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  __shared__ double sums[NS][NVMAX];
+  for (int kv = warp; kv < NS * NV; kv += nwarp) {
+    const int k = kv / NV, v = kv % NV;
+    double s = 0.0;
+    if (j0 + k < nsys) {
+      const double *p = c.partials + ((long long)(j0 + k) * NVMAX + v) * c.pstride;
+      for (int i = lane; i < nbx; i += 32) s += __ldcg(p + i);
+    }
+    s = warp_sum(s);
+    if (lane == 0) sums[k][v] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.grp_ticket[grp] = 0u;
+    for (int k = 0; k < NS; ++k) {
+      const int j = j0 + k;
+      if (j >= nsys) continue;
+      // only systems that took part are finalised (see sys_gate)
+      bool part;
+      {
+        const int done = __ldcg(&c.st[j].done), upd = __ldcg(&c.st[j].update);
+        if (fin == FIN_INIT) part = true;
+        else if (fin == FIN_RESID) part = (done == 0 && upd != 0);
+        else part = (done == 0);
+      }
+      if (part) finalize_system(c, fin, j, sums[k]);
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(c.all_ticket, 1u);
+    if (t == (unsigned)(ngroups - 1)) {
+      *c.all_ticket = 0u;
+      __threadfence();
+      int running = 0, upd = 0;
+      for (int j = 0; j < nsys; ++j) {
+        if (__ldcg(&c.st[j].done) == 0) {
+          running = 1;
+          if (__ldcg(&c.st[j].update)) upd = 1;
+        }
+      }
+      c.flags[0] = running;
+      c.flags[1] = upd;
+      if (c.use_graph_cond) {
+        if (fin == FIN_NORM) cudaGraphSetConditional(c.h_update, (unsigned)upd);
+        if (fin == FIN_NORM || fin == FIN_RESID) cudaGraphSetConditional(c.h_loop, (unsigned)running);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the half operator with fused epilogues
+// ---------------------------------------------------------------------------
+// EPI_PLAIN:     out = D in
+// EPI_MDAGM:     out = m4 center - D in
+// EPI_MDAGM_DOT: as EPI_MDAGM, plus sum_s Re<center, out> per system -> FIN_ALPHA
+// EPI_RESID:     (FP64) out = b - (m4 x - D in), reduced to the output storage,
+//                plus ||b - A x||^2 per system (in FP64) -> FIN_RESID
+template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT>
+__global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
+  typedef typename Tr<LP>::R R;
+  const Geom g = a.g;
+  const int Ve = g.Ve;
+  const int G = a.ngroups;
+  const int grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
+  const int j0 = grp * NS;
+  bool act[NS];
+  R m4[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    act[k] = sys_gate(a.ctl, a.gate, j0 + k, a.nsys);
+    m4[k] = (R)((a.ctl.st != nullptr && j0 + k < a.nsys) ? a.ctl.st[j0 + k].m4 : a.m4_single);
+  }
+  double part[NS][1];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) part[k][0] = 0.0;
+
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) any |= act[k];
+
+  const int s = bx * BT + threadIdx.x;
+  if (any && s < Ve) {
+    const int P = a.par_out;
+    int x[4];
+    site_coords(g, P, s, x);
+    R acc[NS][6];
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc[k][i] = 0;
+
+    const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
+    int eta_bits = 0;  // running sum x_0 + ... + x_{mu-1}
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const R eta = (eta_bits & 1) ? R(-1) : R(1);
+      eta_bits += x[mu];
+      int xf[4] = {x[0], x[1], x[2], x[3]};
+      int xb[4] = {x[0], x[1], x[2], x[3]};
+      xf[mu] = (x[mu] + 1 == Ls[mu]) ? 0 : x[mu] + 1;
+      xb[mu] = (x[mu] == 0) ? Ls[mu] - 1 : x[mu] - 1;
+      const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
+      const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
+      R bf = eta, bb = eta;
+      if (mu == 3 && g.ap) {
+        if (x[3] == g.L3 - 1) bf = -bf;
+        if (x[3] == 0) bb = -bb;
+      }
+      {
+        R u[18];
+        load_link<LP, RECON>(a.links, Ve, P, mu, s, u);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (!act[k]) continue;
+          R v[6];
+          load_vec<VP>(a.in, k + j0, sf, Ve, v);
+          mv_acc(u, v, bf, acc[k]);
+        }
+      }
+      {
+        R u[18];
+        load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, u);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (!act[k]) continue;
+          R v[6];
+          load_vec<VP>(a.in, k + j0, sb, Ve, v);
+          mvdag_acc(u, v, -bb, acc[k]);
+        }
+      }
+    }
+
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (!act[k]) continue;
+      const int j = k + j0;
+      if (EPI == EPI_PLAIN) {
+        store_vec<OP>(a.out, j, s, Ve, acc[k]);
+      } else if (EPI == EPI_MDAGM || EPI == EPI_MDAGM_DOT) {
+        R c[6], o[6];
+        load_vec<VP>(a.center, j, s, Ve, c);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) o[i] = m4[k] * c[i] - acc[k][i];
+        store_vec<OP>(a.out, j, s, Ve, o);
+        if (EPI == EPI_MDAGM_DOT) {
+          R d = 0;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) d += c[i] * o[i];
+          part[k][0] += (double)d;
+        }
+      } else {  // EPI_RESID (R = double)
+        R xx[6], bv[6], o[6];
+        load_vec<P64>(a.center, j, s, Ve, xx);
+        load_vec<P64>(a.aux, j, s, Ve, bv);
+        double nn = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
+          nn += (double)o[i] * (double)o[i];
+        }
+        store_vec<OP>(a.out, j, s, Ve, o);
+        part[k][0] += nn;
+      }
+    }
+  }
+
+  if (EPI == EPI_MDAGM_DOT || EPI == EPI_RESID) {
+    if (a.ctl.st != nullptr) reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused BLAS-1 steps of the CG iteration (one thread per site, NS systems)
+// ---------------------------------------------------------------------------
+// r -= alpha Ap; x += alpha p; ||r||^2 -> FIN_NORM.  p/Ap at VP, r/x at RP.
+template <int VP, int RP, int NS, int BT>
+__global__ void __launch_bounds__(BT) k_axpy_norm(const BlasArgs a) {
+  typedef typename Tr<RP>::R R;
+  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
+  const int j0 = grp * NS, Ve = a.Ve;
+  const int s = bx * BT + threadIdx.x;
+  double part[NS][1];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) part[k][0] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int j = j0 + k;
+    if (!sys_gate(a.ctl, a.gate, j, a.nsys) || s >= Ve) continue;
+    const R alpha = (R)a.ctl.st[j].alpha;
+    R p[6], ap[6], r[6], x[6];
+    load_vec<VP>(a.p, j, s, Ve, p);
+    load_vec<VP>(a.Ap, j, s, Ve, ap);
+    load_vec_rw<RP>(a.r, j, s, Ve, r);
+    load_vec_rw<RP>(a.x, j, s, Ve, x);
+    R nn = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      r[i] -= alpha * ap[i];
+      x[i] += alpha * p[i];
+      nn += r[i] * r[i];
+    }
+    store_vec<RP>(a.r, j, s, Ve, r);
+    store_vec<RP>(a.x, j, s, Ve, x);
+    part[k][0] = (double)nn;
+  }
+  reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+}
+
+// p = r + beta p
+template <int VP, int RP, int NS, int BT>
+__global__ void __launch_bounds__(BT) k_xpay(const BlasArgs a) {
+  typedef typename Tr<RP>::R R;
+  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G;
+  const int j0 = grp * NS, Ve = a.Ve;
+  const int s = bx * BT + threadIdx.x;
+  if (s >= Ve) return;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int j = j0 + k;
+    if (!sys_gate(a.ctl, a.gate, j, a.nsys)) continue;
+    const R beta = (R)a.ctl.st[j].beta;
+    R p[6], r[6];
+    load_vec_rw<VP>(a.p, j, s, Ve, p);
+    load_vec<RP>(a.r, j, s, Ve, r);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) p[i] = r[i] + beta * p[i];
+    store_vec<VP>(a.p, j, s, Ve, p);
+  }
+}
+
+// reliable update, part 1: x64 += x_lo; x_lo = 0 (systems with an update due)
+template <int RP, int NS, int BT>
+__global__ void __launch_bounds__(BT) k_accum_x(const BlasArgs a) {
+  typedef typename Tr<RP>::R R;
+  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G;
+  const int j0 = grp * NS, Ve = a.Ve;
+  const int s = bx * BT + threadIdx.x;
+  if (s >= Ve) return;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int j = j0 + k;
+    if (!sys_gate(a.ctl, a.gate, j, a.nsys)) continue;
+    R xl[6];
+    double x6[6];
+    load_vec_rw<RP>(a.x, j, s, Ve, xl);
+    load_vec_rw<P64>(a.x64, j, s, Ve, x6);
+    const R z[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x6[i] += (double)xl[i];
+    store_vec<P64>(a.x64, j, s, Ve, x6);
+    store_vec<RP>(a.x, j, s, Ve, z);
+  }
+}
+
+// CG start: x64 = 0, x_lo = 0, r = round(b), p = round(r);
+// partials ||b||^2 (FP64) and ||r||^2 -> FIN_INIT
+template <int VP, int RP, int NS, int BT>
+__global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
+  typedef typename Tr<RP>::R R;
+  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
+  const int j0 = grp * NS, Ve = a.Ve;
+  const int s = bx * BT + threadIdx.x;
+  double part[NS][2];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) part[k][0] = part[k][1] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int j = j0 + k;
+    if (j >= a.nsys || s >= Ve) continue;
+    double b[6];
+    load_vec<P64>(a.b, j, s, Ve, b);
+    double bb = 0.0;
+    R r[6];
+    const double z64[6] = {0, 0, 0, 0, 0, 0};
+    const R z[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      bb += b[i] * b[i];
+      r[i] = (R)b[i];
+    }
+    store_vec<RP>(a.r, j, s, Ve, r);
+    R rr_[6];
+    load_vec_rw<RP>(a.r, j, s, Ve, rr_);  // the values the iteration sees
+    R rr = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) rr += rr_[i] * rr_[i];
+    store_vec<VP>(a.p, j, s, Ve, rr_);
+    store_vec<RP>(a.x, j, s, Ve, z);
+    store_vec<P64>(a.x64, j, s, Ve, z64);
+    part[k][0] = bb;
+    part[k][1] = (double)rr;
+  }
+  reduce_and_finalize<NS, 2>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion between the ABI's [Ve][3] FP64 complex and the device SoA
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void k_pack_vec(const double2 *__restrict__ src, VecArg dst, int k, int Ve) {
+  typedef typename Tr<P>::R R;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Ve) return;
+  R v[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double2 w = src[(long long)s * 3 + c];
+    v[2 * c] = (R)w.x;
+    v[2 * c + 1] = (R)w.y;
+  }
+  store_vec<P>(dst, k, s, Ve, v);
+}
+
+template <int P>
+__global__ void k_unpack_vec(VecArg src, int k, double2 *__restrict__ dst, int Ve) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Ve) return;
+  double v[6];
+  {
+    typename Tr<P>::R w[6];
+    load_vec_rw<P>(src, k, s, Ve, w);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = (double)w[i];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dst[(long long)s * 3 + c] = make_double2(v[2 * c], v[2 * c + 1]);
+}
+
+// dst = src re-stored at another precision (FP16/BF16 quantise per site)
+template <int PIN, int POUT>
+__global__ void k_convert_vec(VecArg src, VecArg dst, int nsys, int Ve) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nsys * Ve) return;
+  const int k = (int)(i / Ve), s = (int)(i % Ve);
+  typename Tr<POUT>::R v[6];
+  load_vec_rw<PIN>(src, k, s, Ve, v);
+  store_vec<POUT>(dst, k, s, Ve, v);
+}
+
+// canonical [4][V][3][3] FP64 links -> [2][4][NE][Ve] at precision LP
+// (FP16/BF16 links are stored unscaled: |U_ij| <= 1 for SU(3))
+template <int LP, int RECON>
+__global__ void k_pack_links(const double2 *__restrict__ src, void *dst, Geom g) {
+  typedef typename Tr<LP>::S2 S2;
+  typedef typename Tr<LP>::R R;
+  constexpr int NE = RECON ? 6 : 9;
+  const long long V = 2ll * g.Ve;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over 4 V links
+  if (i >= 4 * V) return;
+  const int mu = (int)(i / V);
+  const long long lex = i % V;
+  int x0 = (int)(lex % g.L0);
+  long long r = lex / g.L0;
+  const int x1 = (int)(r % g.L1);
+  r /= g.L1;
+  const int x2 = (int)(r % g.L2);
+  const int x3 = (int)(r / g.L2);
+  const int par = (x0 + x1 + x2 + x3) & 1;
+  const int s = (int)(lex >> 1);
+  S2 *d = reinterpret_cast<S2 *>(dst) + (long long)((par * 4 + mu) * NE) * g.Ve + s;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const double2 w = src[i * 9 + e];
+    R re, im;
+    if (LP == P64) {
+      re = (R)w.x;
+      im = (R)w.y;
+    } else {
+      // FP64 -> FP32 first; FP16/BF16 round that FP32 value
+      re = (R)__double2float_rn(w.x);
+      im = (R)__double2float_rn(w.y);
+    }
+    d[(long long)e * g.Ve] = from_r<LP>(re, im);
+  }
+}
+
+// unitarity and determinant defect of every link -> max into *out (as bits of a
+// non-negative double, so an integer atomicMax orders them)
+__global__ void k_su3_defect(const double2 *__restrict__ U, long long nlinks, unsigned long long *out);
+
+}  // namespace stag

@@ -1,0 +1,260 @@
+"""ctypes binding of libstag.so: the functions of include/stag.h under the same names.
+
+Argument marshalling only -- every step of the computation runs in the CUDA
+library.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays, C
+contiguous, dtype complex128 (or float64 with a trailing (re, im) axis).  A
+missing library raises; there is no CPU fallback.
+
+Layouts (see include/stag.h): links (4, V, 3, 3) complex128 with V in
+lexicographic order (x fastest); checkerboard vectors (V/2, 3) complex128.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STAG_OK = 0
+STAG_NOT_CONVERGED = 1
+STAG_ERR_ARG = -1
+STAG_ERR_CUDA = -2
+STAG_ERR_OOM = -3
+STAG_ERR_NOT_SU3 = -4
+STAG_ERR_BREAKDOWN = -5
+STAG_ERR_STATE = -7
+
+STAG_FP64, STAG_FP32, STAG_FP16, STAG_BF16 = 0, 1, 2, 3
+STAG_ROUND_OUTPUT = 0x100
+STAG_ANTIPERIODIC_T = 1
+STAG_RECON12 = 2
+
+PRECISIONS = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "bf16": STAG_BF16}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class StagError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libstag.so (built by __graft_entry__.build() / paper_1511_00088_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libstag.so not built ({path}); run paper_1511_00088_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "stag_create": (I, [ctypes.POINTER(ctypes.c_int), I, P, PP]),
+            "stag_destroy": (I, [P]),
+            "stag_links_upload": (I, [P, P]),
+            "stag_dslash_oe": (I, [P, I, P, P]),
+            "stag_dslash_eo": (I, [P, I, P, P]),
+            "stag_mdagm": (I, [P, I, D, P, P]),
+            "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
+            "stag_time_dslash": (I, [P, I, I, P, P]),
+            "stag_last_error": (ctypes.c_char_p, [P]),
+            "stag_status_string": (ctypes.c_char_p, [I]),
+            "stag_abi_version": (I, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().stag_status_string(int(status)).decode()
+    except Exception:  # noqa: BLE001 - naming a status must not raise
+        return f"status {status}"
+
+
+def _ptr(a):
+    """Raw pointer of a contiguous complex128/float64 torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if a.dtype not in (torch.complex128, torch.float64):
+                raise ValueError("tensor must be complex128 or float64")
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C contiguous")
+        if a.dtype not in (np.complex128, np.float64):
+            raise ValueError("array must be complex128 or float64")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+# ---------------------------------------------------------------------------
+# the C functions under their own names (return the status code)
+# ---------------------------------------------------------------------------
+def stag_create(dims, flags=STAG_ANTIPERIODIC_T, cuda_stream=None):
+    lib = load()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    h = ctypes.c_void_p()
+    st = lib.stag_create(d, int(flags), ctypes.c_void_p(cuda_stream or 0), ctypes.byref(h))
+    return st, h
+
+
+def stag_destroy(ctx):
+    return load().stag_destroy(ctx)
+
+
+def stag_links_upload(ctx, links):
+    return load().stag_links_upload(ctx, _ptr(links))
+
+
+def stag_dslash_oe(ctx, precision, in_even, out_odd):
+    return load().stag_dslash_oe(ctx, int(precision), _ptr(in_even), _ptr(out_odd))
+
+
+def stag_dslash_eo(ctx, precision, in_odd, out_even):
+    return load().stag_dslash_eo(ctx, int(precision), _ptr(in_odd), _ptr(out_even))
+
+
+def stag_mdagm(ctx, precision, mass, in_even, out_even):
+    return load().stag_mdagm(ctx, int(precision), float(mass), _ptr(in_even), _ptr(out_even))
+
+
+def stag_cg_solve(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, true_res=None):
+    """srcs: list of nrhs vectors; xs: list of nrhs*nmass output vectors (slot r*nmass+k)."""
+    lib = load()
+    nrhs, nmass = len(srcs), len(masses)
+    sp = (ctypes.c_void_p * nrhs)(*[_ptr(s) for s in srcs])
+    xp = (ctypes.c_void_p * (nrhs * nmass))(*[_ptr(x) for x in xs])
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    it = np.zeros(nrhs * nmass, np.int32) if iters is None else iters
+    tr = np.zeros(nrhs * nmass, np.float64) if true_res is None else true_res
+    st = lib.stag_cg_solve(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
+                           int(precision), xp, it.ctypes.data, tr.ctypes.data)
+    return st, it, tr
+
+
+def stag_time_dslash(ctx, precision, nlaunch):
+    ms = ctypes.c_double(0.0)
+    by = ctypes.c_double(0.0)
+    st = load().stag_time_dslash(ctx, int(precision), int(nlaunch), ctypes.byref(ms), ctypes.byref(by))
+    return st, ms.value, by.value
+
+
+def stag_last_error(ctx):
+    return load().stag_last_error(ctx).decode()
+
+
+def stag_status_string(status):
+    return load().stag_status_string(int(status)).decode()
+
+
+def stag_abi_version():
+    return load().stag_abi_version()
+
+
+# ---------------------------------------------------------------------------
+# a small object wrapper that raises on errors
+# ---------------------------------------------------------------------------
+class Context:
+    """One lattice on the current CUDA device (see stag_create)."""
+
+    def __init__(self, dims, antiperiodic=True, recon12=False, stream=None):
+        flags = (STAG_ANTIPERIODIC_T if antiperiodic else 0) | (STAG_RECON12 if recon12 else 0)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:  # noqa: BLE001
+                stream = 0
+        st, h = stag_create(dims, flags, stream)
+        if st != STAG_OK:
+            raise StagError(st, "stag_create failed")
+        self.h = h
+        self.dims = tuple(int(v) for v in dims)
+        self.V = int(np.prod(self.dims))
+        self.Ve = self.V // 2
+
+    def _check(self, st, ok=(STAG_OK,)):
+        if st not in ok:
+            raise StagError(st, stag_last_error(self.h))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            stag_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def links_upload(self, links):
+        return self._check(stag_links_upload(self.h, links))
+
+    def _like(self, a):
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                return torch.empty((self.Ve, 3), dtype=torch.complex128, device=a.device)
+        except ImportError:  # pragma: no cover
+            pass
+        return np.empty((self.Ve, 3), np.complex128)
+
+    def dslash_oe(self, x, precision=STAG_FP64, out=None):
+        out = self._like(x) if out is None else out
+        self._check(stag_dslash_oe(self.h, precision, x, out))
+        return out
+
+    def dslash_eo(self, x, precision=STAG_FP64, out=None):
+        out = self._like(x) if out is None else out
+        self._check(stag_dslash_eo(self.h, precision, x, out))
+        return out
+
+    def mdagm(self, x, mass, precision=STAG_FP64, out=None):
+        out = self._like(x) if out is None else out
+        self._check(stag_mdagm(self.h, precision, mass, x, out))
+        return out
+
+    def cg_solve(self, srcs, masses, tol=1e-10, maxiter=100000, precision=STAG_FP32, xs=None,
+                 allow_not_converged=False):
+        """Returns (xs, status, iters, true_res); xs[r * nmass + k] solves source r, mass k."""
+        if xs is None:
+            xs = [self._like(srcs[r]) for r in range(len(srcs)) for _ in masses]
+        st, it, tr = stag_cg_solve(self.h, srcs, masses, tol, maxiter, precision, xs)
+        ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
+        self._check(st, ok)
+        return xs, st, it, tr
+
+    def time_dslash(self, precision=STAG_FP32, nlaunch=50):
+        st, ms, by = stag_time_dslash(self.h, precision, nlaunch)
+        self._check(st)
+        return ms, by

@@ -1,0 +1,181 @@
+"""GPU CG solves (FP64 and mixed precision with reliable updates) against the oracle.
+
+The bar for every solve: the true FP64 residual ||b - A x|| / ||b||, recomputed
+by the CPU oracle on the returned x, is <= 1e-10, and the library's own FP64
+true residual agrees with it.  The solution matches the oracle's CG solution to
+the accuracy the condition number allows.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1511_00088_gb300 import stag, synth
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp64": stag.STAG_FP64, "fp32": stag.STAG_FP32, "fp16": stag.STAG_FP16, "bf16": stag.STAG_BF16}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1511_00088_gb300 import build
+    build.build()
+    stag.load()
+    assert torch.cuda.is_available()
+
+
+def check_solution(L, U, m, b, x, tr_gpu, tol=1e-10):
+    tr = oracle.true_residual(L, U, m, b, x)
+    assert tr <= tol, tr
+    assert abs(tr_gpu - tr) <= 1e-12 + 0.05 * tr, (tr_gpu, tr)
+    return tr
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_config0_8x4(prec):
+    """8^4, links exp(0.3 i H), m = 0.05, one Gaussian source, tol 1e-10."""
+    L = (8, 8, 8, 8)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.3, 1)
+    b = synth.gaussian_vector(V // 2, 2)
+    m = 0.05
+    xo, st_o, it_o, tr_o = oracle.cg(L, U, m, b, tol=1e-12)
+    assert st_o == 0
+    with stag.Context(L) as ctx:
+        ctx.links_upload(U)
+        xs, st, it, tr = ctx.cg_solve([b], [m], tol=1e-10, maxiter=5000, precision=PREC[prec])
+    x = xs[0]
+    check_solution(L, U, m, b, x, tr[0])
+    kappa = (4 * m * m + 16) / (4 * m * m)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= kappa * 1e-10
+    # iteration count in the range of plain CG (mixed: reliable updates may add a few)
+    assert it[0] <= 3 * it_o + 20, (it[0], it_o)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("L", [(4, 2, 6, 8), (6, 6, 6, 12), (2, 2, 2, 2)])
+def test_odd_shapes_device_buffers(prec, L):
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 11)
+    b = synth.gaussian_vector(V // 2, 12)
+    m = 0.1
+    with stag.Context(L) as ctx:
+        ctx.links_upload(torch.from_numpy(U).cuda())
+        xs, st, it, tr = ctx.cg_solve([torch.from_numpy(b).cuda()], [m], tol=1e-10, maxiter=5000,
+                                      precision=PREC[prec])
+        torch.cuda.synchronize()
+    check_solution(L, U, m, b, xs[0].cpu().numpy(), tr[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_multi_rhs_multi_mass(prec):
+    """3 sources x 3 masses in one solve: every system to 1e-10 (per-system
+    alpha, beta, reliable updates and convergence masks)."""
+    L = (6, 4, 4, 8)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 21)
+    bs = [synth.gaussian_vector(V // 2, 22 + r) for r in range(3)]
+    masses = [0.02, 0.05, 0.3]
+    with stag.Context(L) as ctx:
+        ctx.links_upload(U)
+        xs, st, it, tr = ctx.cg_solve(bs, masses, tol=1e-10, maxiter=8000, precision=PREC[prec])
+    for r in range(3):
+        for k, m in enumerate(masses):
+            j = r * len(masses) + k
+            check_solution(L, U, m, bs[r], xs[j], tr[j])
+    # heavier mass converges in fewer iterations
+    assert it[2] < it[0]
+
+
+def test_batch_of_nine_matches_single_solves():
+    """The batched kernels (several systems per thread) give the same solutions
+    as one-system solves, to the solve tolerance."""
+    L = (4, 4, 4, 8)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 31)
+    bs = [synth.gaussian_vector(V // 2, 32 + r) for r in range(9)]
+    m = 0.05
+    with stag.Context(L) as ctx:
+        ctx.links_upload(U)
+        xb, st, it, tr = ctx.cg_solve(bs, [m], tol=1e-11, maxiter=5000, precision=stag.STAG_FP32)
+        for r in (0, 4, 8):
+            xs, _, _, _ = ctx.cg_solve([bs[r]], [m], tol=1e-11, maxiter=5000, precision=stag.STAG_FP32)
+            assert np.linalg.norm(xs[0] - xb[r]) / np.linalg.norm(xs[0]) < 1e-7
+
+
+def test_zero_source_and_iteration_cap():
+    L = (4, 4, 4, 4)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 41)
+    z = np.zeros((V // 2, 3), np.complex128)
+    b = synth.gaussian_vector(V // 2, 42)
+    with stag.Context(L) as ctx:
+        ctx.links_upload(U)
+        xs, st, it, tr = ctx.cg_solve([z, b], [0.1], tol=1e-10, maxiter=3000, precision=stag.STAG_FP32)
+        assert st == stag.STAG_OK
+        assert it[0] == 0 and tr[0] == 0.0 and np.all(xs[0] == 0)
+        check_solution(L, U, 0.1, b, xs[1], tr[1])
+        xs, st, it, tr = ctx.cg_solve([b], [0.01], tol=1e-10, maxiter=3, precision=stag.STAG_FP32,
+                                      allow_not_converged=True)
+        assert st == stag.STAG_NOT_CONVERGED and it[0] == 3
+        # the returned x is the FP64-accumulated iterate with its true residual
+        assert abs(oracle.true_residual(L, U, 0.01, b, xs[0]) - tr[0]) <= 1e-6 * tr[0]
+
+
+def test_bad_arguments():
+    L = (4, 4, 4, 4)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 51)
+    b = synth.gaussian_vector(V // 2, 52)
+    x = np.empty_like(b)
+    st, h = stag.stag_create(L, stag.STAG_ANTIPERIODIC_T, 0)
+    try:
+        assert stag.stag_cg_solve(h, [b], [0.1], 1e-10, 100, stag.STAG_FP32, [x])[0] == stag.STAG_ERR_STATE
+        stag.stag_links_upload(h, U)
+        assert stag.stag_cg_solve(h, [b], [0.1], 0.0, 100, stag.STAG_FP32, [x])[0] == stag.STAG_ERR_ARG
+        assert stag.stag_cg_solve(h, [b], [0.1], 1e-10, 0, stag.STAG_FP32, [x])[0] == stag.STAG_ERR_ARG
+        assert stag.stag_cg_solve(h, [b], [0.1], 1e-10, 100, 9, [x])[0] == stag.STAG_ERR_ARG
+        assert stag.stag_cg_solve(h, [b], [float("nan")], 1e-10, 100, 1, [x])[0] == stag.STAG_ERR_ARG
+    finally:
+        stag.stag_destroy(h)
+
+
+def test_deterministic_and_graph_equals_eager():
+    """Fixed-order reductions: repeated solves are bit-identical, and the
+    graph-launched solve equals the eagerly launched one."""
+    L = (6, 6, 6, 12)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 61)
+    b = synth.gaussian_vector(V // 2, 62)
+    with stag.Context(L) as ctx:
+        ctx.links_upload(U)
+        x1, _, it1, _ = ctx.cg_solve([b], [0.03], precision=stag.STAG_FP32)
+        x2, _, it2, _ = ctx.cg_solve([b], [0.03], precision=stag.STAG_FP32)
+    assert np.array_equal(x1[0], x2[0]) and it1[0] == it2[0]
+    os.environ["STAG_EAGER"] = "1"
+    try:
+        with stag.Context(L) as ctx:
+            ctx.links_upload(U)
+            x3, _, it3, _ = ctx.cg_solve([b], [0.03], precision=stag.STAG_FP32)
+    finally:
+        del os.environ["STAG_EAGER"]
+    assert np.array_equal(x1[0], x3[0]) and it1[0] == it3[0]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_config1_production_lattice(prec):
+    """20^3 x 64, links exp(0.4 i H), m = 0.01: the benchmark's workload."""
+    L = (20, 20, 20, 64)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 1001)
+    b = synth.gaussian_vector(V // 2, 1002)
+    m = 0.01
+    with stag.Context(L) as ctx:
+        ctx.links_upload(torch.from_numpy(U).cuda())
+        xs, st, it, tr = ctx.cg_solve([torch.from_numpy(b).cuda()], [m], tol=1e-10, maxiter=20000,
+                                      precision=PREC[prec])
+        torch.cuda.synchronize()
+    check_solution(L, U, m, b, xs[0].cpu().numpy(), tr[0])
