@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the mixed-precision staggered CG (Sec. 3 of the paper) on one GB300.
+
+A step is one solve of (4 m^2 - D_eo D_oe) x = b to a true FP64 residual of
+1e-10 on a 20^3 x 64 lattice (the paper's production shape; synthetic SU(3)
+links exp(0.4 i H), m = 0.01, one complex-Gaussian source), FP32 inner
+iteration with FP64 reliable updates, through the C ABI (libstag.so).
+
+Printed (rank 0, one JSON line):
+  value       CG GFLOP/s = 1212 flop x V/2 sites x iterations / solve time,
+              inputs resident in HBM, CUDA events on the solver's stream,
+              L2 flushed (256 MiB write) before every timed solve;
+  e2e         the same metric through the C ABI with the source in pinned host
+              memory and the solution copied back, copies inside the timing;
+  roofline    the dominant kernel (the FP32 half operator D_oe) against the
+              measured HBM copy bandwidth;
+  cpu_baseline the FP64 CPU oracle's CG on a bounded sample of the workload.
+Extra keys give time-to-solution of the mixed, FP16/BF16-storage and plain FP64
+solves on the same GPU.
+
+--impl reference times the CPU oracle as the reference arm.
+Multi-GPU (torchrun): independent replicas, each rank its own source (weak
+scaling); no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s & HBM GB/s; CG time-to-1e-10 residual, mixed/batched vs FP64"
+FLOP_PER_SITE_ITER = 1212     # 2 x 570 (two half operators) + 12 (mass) + 5 x 12 (BLAS-1)
+DSLASH_FLOP_PER_SITE = 570    # 8 x 66 (SU(3) x vector) + 7 x 6 (accumulation)
+PAPER_TX_CG_GFLOPS = 107.7    # Titan X, mixed CG, 20^3 x 64, one GPU (Table 2 of the paper)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lattice", default="20,20,20,64")
+    ap.add_argument("--mass", type=float, default=0.01)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="profiling runs: skip the comparison solves, the e2e leg and the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(L, mass, tol, prec):
+    return {
+        "workload": f"{L[0]}^3x{L[3]} even-odd staggered CG, {prec.upper()} inner iteration, "
+                    f"FP64 reliable updates (delta=0.1), m={mass}, 1 RHS, true residual {tol:g}"
+        if L[0] == L[1] == L[2] else f"{L} staggered CG",
+        "lattice": list(L),
+        "links": "reunitarised exp(0.4 i H), synthetic (stands in for the MILC 20^3x64 ensemble)",
+        "mass": mass,
+        "tol": tol,
+        "inner_precision": prec,
+        "reliable_update": "f64",
+        "l2": "flushed before every timed solve (256 MiB write); link field 147 MB > L2",
+        "graph": "one CUDA graph launch per solve (conditional WHILE/IF nodes)",
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("stag_kernels.cuh", "dslash_p32.cu", "dslash_inst.cuh", "launch.h"):
+        with open(os.path.join(ROOT, "paper_1511_00088_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per launch of `key` from the committed ncu summary, when it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == key and parts[1] == cur:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_oracle_sample(L, U, b, mass, budget_s):
+    """The FP64 oracle's CG for a bounded number of iterations on this workload."""
+    import oracle
+    t = time.perf_counter()
+    oracle.mdagm(L, U, mass, b)
+    t1 = time.perf_counter() - t
+    n = max(2, int(budget_s / max(t1, 1e-3)))
+    t = time.perf_counter()
+    _, st, it, _ = oracle.cg(L, U, mass, b, tol=1e-300, maxiter=n)
+    dt = time.perf_counter() - t
+    Ve = (L[0] * L[1] * L[2] * L[3]) // 2
+    # the oracle also recomputes the true residual once (one more operator application)
+    gflops = FLOP_PER_SITE_ITER * Ve * it / dt / 1e9
+    return gflops, it, dt
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from paper_1511_00088_gb300 import synth
+    L = tuple(int(v) for v in args.lattice.split(","))
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, synth.seed_for(1, 1))
+    b = synth.gaussian_vector(V // 2, synth.seed_for(1, 2))
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        g, it, dt = cpu_oracle_sample(L, U, b, args.mass, 6.0)
+        if i >= args.warmup:
+            vals.append(g)
+            times.append(dt)
+    value = statistics.mean(vals)
+    sample = f"{it} FP64 CG iterations of the CPU oracle per step on the {L} field, single thread"
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": workload_config(L, args.mass, args.tol, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1511_00088_gb300 import build as B
+    from paper_1511_00088_gb300 import stag, synth
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    stag.load()
+    prec = stag.PRECISIONS[args.precision]
+    L = tuple(int(v) for v in args.lattice.split(","))
+    V = synth.volume(L)
+    Ve = V // 2
+    U = synth.random_links(L, 0.4, synth.seed_for(1, 1))
+    b = synth.gaussian_vector(Ve, synth.seed_for(1, 2 + rank))
+    stream = torch.cuda.current_stream()
+    ctx = stag.Context(L, stream=stream.cuda_stream)
+    ctx.links_upload(torch.from_numpy(U).cuda())
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.empty_like(bd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve():
+        xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=50000,
+                                      precision=prec, xs=[xd])
+        return int(it[0]), float(tr[0])
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    total_ms, iters, updates, launches, res = 0.0, [], [], 0, []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, tr = solve()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        _, nu, _ = ctx.solve_stats(0)
+        iters.append(it)
+        updates.append(nu)
+        res.append(tr)
+        # pack + init + unpack, 4 kernels per iteration, 3 per reliable update
+        launches += 3 + 4 * it + 3 * nu
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = total_ms / args.steps
+    flops_step = FLOP_PER_SITE_ITER * Ve * statistics.mean(iters)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        f = torch.tensor([flops_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        flops_all = float(f.item())
+    else:
+        flops_all = flops_step
+    value = flops_all / (ms_step * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    e2e_ms, e2e_it = [], []
+    for k in range(0 if args.no_extras else max(1, min(args.steps, 5))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        xs, st, it, tr = ctx.cg_solve([bh], [args.mass], tol=args.tol, maxiter=50000,
+                                      precision=prec, xs=[xh])
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+        e2e_it.append(int(it[0]))
+    e2e_ms_step = statistics.mean(e2e_ms) if e2e_ms else None
+    e2e_value = (FLOP_PER_SITE_ITER * Ve * statistics.mean(e2e_it) / (e2e_ms_step * 1e-3) / 1e9
+                 if e2e_ms else None)
+    if dist and e2e_value is not None:
+        t = torch.tensor([e2e_value], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_value = float(t.item())
+
+    # dominant kernel: the half operator D_oe at the inner precision, CUDA events
+    ms_ds, bytes_ds = ctx.time_dslash(prec, nlaunch=200)
+    hbm, peak_kind = peaks()
+    achieved = bytes_ds / (ms_ds * 1e-3) / 1e9
+    key = f"dslash_oe_{args.precision}_{'x'.join(map(str, L))}"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": ncu_traffic(key), "peak_source": peak_kind,
+            "kernel": f"k_dslash (D_oe, {args.precision}, 1 RHS)", "ms_per_launch": ms_ds,
+            "algorithmic_bytes_per_launch": bytes_ds,
+            "dslash_gflops": DSLASH_FLOP_PER_SITE * Ve / (ms_ds * 1e-3) / 1e9}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16),
+                        ("fp32", stag.STAG_FP32)):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=50000, precision=p,
+                                          xs=[xd])
+            e1.record(stream)
+            e1.synchronize()
+            _, nu, _ = ctx.solve_stats(0)
+            extras[f"cg_{name}"] = {"ms": e0.elapsed_time(e1), "iters": int(it[0]),
+                                    "reliable_updates": nu, "true_res": float(tr[0])}
+        for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16)):
+            m, by = ctx.time_dslash(p, nlaunch=50)
+            extras[f"dslash_{name}"] = {"ms": m, "GB/s": by / (m * 1e-3) / 1e9,
+                                        "GFLOP/s": DSLASH_FLOP_PER_SITE * Ve / (m * 1e-3) / 1e9}
+        extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps)
+
+    cpu = None
+    if ws == 1 and rank == 0 and not args.no_extras:
+        g, it, dt = cpu_oracle_sample(L, U, b, args.mass, 12.0)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{it} FP64 CG iterations of the CPU oracle on the same {L} field "
+                         f"({dt:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_TX_CG_GFLOPS,
+            "dtype": "f32" if args.precision == "fp32" else args.precision.replace("fp", "f"),
+            "data": "synthetic", "config": workload_config(L, args.mass, args.tol, args.precision),
+            "time_to_solution_ms": ms_step, "iters": iters[-1], "reliable_updates": updates[-1],
+            "true_res": max(res),
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve,
+                    "d2h_bytes_per_step": 48 * Ve, "ms_per_step": e2e_ms_step},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

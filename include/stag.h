@@ -146,6 +146,16 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
 int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_launch,
                      double *bytes_per_launch);
 
+/*
+ * Statistics of system `sys` (0 <= sys < nrhs * nmass) of the most recent
+ * stag_cg_solve on this context: iterations, FP64 reliable updates (the
+ * recomputations of the residual, including the final one) and the final true
+ * residual.  Any output pointer may be NULL.  STAG_ERR_ARG for a bad index or
+ * before the first solve.
+ */
+int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_updates,
+                     double *true_res);
+
 /* Message of the last error on this context ("" when none). */
 const char *stag_last_error(const stag_ctx *ctx);
 

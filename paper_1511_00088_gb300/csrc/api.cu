@@ -161,6 +161,7 @@ struct stag_ctx {
   VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
   DevBuf defect;
   Work w;
+  int last_nsys = 0;  // systems of the most recent solve (stats in w.h_st)
 };
 
 namespace {
@@ -257,6 +258,7 @@ int work_prepare(stag_ctx *c, int nsys, int prec) {
   const int recon = link_recon(c, prec);
   if (w.nsys == nsys && w.prec == prec && w.recon == recon) return STAG_OK;
   w.drop_graph();
+  c->last_nsys = 0;
   w.nsys = nsys;
   w.prec = prec;
   w.recon = recon;
@@ -545,6 +547,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
   for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
   CK(cudaStreamSynchronize(c->stream));
 
+  c->last_nsys = nsys;
   int status = STAG_OK;
   for (int j = 0; j < nsys; ++j) {
     if (iters) iters[j] = hs[j].iter;
@@ -756,6 +759,15 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updates, double *true_res) {
+  if (!c || c->last_nsys <= 0 || sys < 0 || sys >= c->last_nsys) return STAG_ERR_ARG;
+  const SysState *hs = (const SysState *)c->w.h_st.p;
+  if (iters) *iters = hs[sys].iter;
+  if (reliable_updates) *reliable_updates = hs[sys].n_updates;
+  if (true_res) *true_res = hs[sys].true_res;
+  return STAG_OK;
 }
 
 int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_launch,

@@ -69,6 +69,7 @@ def load():
             "stag_mdagm": (I, [P, I, D, P, P]),
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
+            "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_last_error": (ctypes.c_char_p, [P]),
             "stag_status_string": (ctypes.c_char_p, [I]),
             "stag_abi_version": (I, []),
@@ -159,6 +160,14 @@ def stag_time_dslash(ctx, precision, nlaunch):
     by = ctypes.c_double(0.0)
     st = load().stag_time_dslash(ctx, int(precision), int(nlaunch), ctypes.byref(ms), ctypes.byref(by))
     return st, ms.value, by.value
+
+
+def stag_solve_stats(ctx, sys):
+    it = ctypes.c_int(0)
+    nu = ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    st = load().stag_solve_stats(ctx, int(sys), ctypes.byref(it), ctypes.byref(nu), ctypes.byref(tr))
+    return st, it.value, nu.value, tr.value
 
 
 def stag_last_error(ctx):
@@ -253,6 +262,12 @@ class Context:
         ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
         self._check(st, ok)
         return xs, st, it, tr
+
+    def solve_stats(self, sys=0):
+        """(iters, reliable_updates, true_res) of system `sys` of the last solve."""
+        st, it, nu, tr = stag_solve_stats(self.h, sys)
+        self._check(st)
+        return it, nu, tr
 
     def time_dslash(self, precision=STAG_FP32, nlaunch=50):
         st, ms, by = stag_time_dslash(self.h, precision, nlaunch)
