@@ -335,12 +335,13 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=50000, precision=p,
-                                          xs=[xd])
+                                          xs=[xd], allow_not_converged=True)
             e1.record(stream)
             e1.synchronize()
             _, nu, _ = ctx.solve_stats(0)
             extras[f"cg_{name}"] = {"ms": e0.elapsed_time(e1), "iters": int(it[0]),
-                                    "reliable_updates": nu, "true_res": float(tr[0])}
+                                    "reliable_updates": nu, "true_res": float(tr[0]),
+                                    "status": stag.status_name(st)}
         for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16)):
             m, by = ctx.time_dslash(p, nlaunch=50)
             extras[f"dslash_{name}"] = {"ms": m, "GB/s": by / (m * 1e-3) / 1e9,
