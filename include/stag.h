@@ -156,6 +156,26 @@ int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_l
 int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_updates,
                      double *true_res);
 
+/*
+ * out_even = (4 m^2 - D_eo D_oe) in_even in FP64, with tmp_odd = D_oe in_even
+ * and *dot = Re<in_even, out_even> (FP64, fixed-order reduction), for callers
+ * that cannot allocate device memory (their memory is owned by another
+ * allocator, or they must not allocate once set up).  The paper has no
+ * counterpart of this entry point; it is an interface convenience.
+ * It allocates nothing: every pointer is caller-owned device memory in the
+ * layouts above (dot: one double, may be NULL), and the reduction scratch is a
+ * fixed file-scope device array (512 KiB + 256 B per GPU, held until exit).
+ *   - lattices with more than 8 388 608 sites per parity: STAG_ERR_ARG;
+ *   - the first call on a device looks up that array's address (once per
+ *     device); make it before any stream capture;
+ *   - all calls share the array: calls that overlap on the GPU race;
+ *   - asynchronous: results are ready when the context's stream reaches them.
+ * Errors: STAG_ERR_ARG (size, NULL or host pointer), STAG_ERR_STATE (no links),
+ * STAG_ERR_CUDA.
+ */
+int stag_mdagm_dot_noalloc(stag_ctx *ctx, double mass, const double *in_even, double *tmp_odd,
+                           double *out_even, double *dot);
+
 /* Message of the last error on this context ("" when none). */
 const char *stag_last_error(const stag_ctx *ctx);
 

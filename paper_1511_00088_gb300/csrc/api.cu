@@ -619,6 +619,21 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
 
 }  // namespace
 
+// Internal accessors used by noalloc.cu (not part of the C ABI).
+namespace stag {
+int ctx_fp64_links(const stag_ctx *c, const void **links, Geom *g, cudaStream_t *stream, int *device) {
+  if (!c->have_links) return STAG_ERR_STATE;
+  *links = c->links64.p;
+  *g = c->g;
+  *stream = c->stream;
+  *device = c->device;
+  return STAG_OK;
+}
+void ctx_set_error(stag_ctx *c, const char *msg) { c->err = msg; }
+Geom ctx_geom(const stag_ctx *c) { return c->g; }
+int ctx_device(const stag_ctx *c) { return c->device; }
+}  // namespace stag
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

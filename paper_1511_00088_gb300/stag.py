@@ -70,6 +70,7 @@ def load():
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_solve_stats": (I, [P, I, P, P, P]),
+            "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_last_error": (ctypes.c_char_p, [P]),
             "stag_status_string": (ctypes.c_char_p, [I]),
             "stag_abi_version": (I, []),
@@ -168,6 +169,12 @@ def stag_solve_stats(ctx, sys):
     tr = ctypes.c_double(0.0)
     st = load().stag_solve_stats(ctx, int(sys), ctypes.byref(it), ctypes.byref(nu), ctypes.byref(tr))
     return st, it.value, nu.value, tr.value
+
+
+def stag_mdagm_dot_noalloc(ctx, mass, in_even, tmp_odd, out_even, dot=None):
+    """No-allocation M^dag M with FP64 <in, out>; every argument a CUDA tensor."""
+    return load().stag_mdagm_dot_noalloc(ctx, float(mass), _ptr(in_even), _ptr(tmp_odd), _ptr(out_even),
+                                         None if dot is None else _ptr(dot))
 
 
 def stag_last_error(ctx):
