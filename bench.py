@@ -329,12 +329,12 @@ def run_ours(args):
     extras = {}
     if not args.no_extras and rank == 0:
         for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16),
-                        ("fp32", stag.STAG_FP32)):
+                        ("fp32", stag.STAG_FP32), ("fp16_half_vectors", stag.STAG_FP16 | stag.STAG_HALF_VECTORS)):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=50000, precision=p,
+            xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=30000, precision=p,
                                           xs=[xd], allow_not_converged=True)
             e1.record(stream)
             e1.synchronize()

@@ -61,6 +61,12 @@ extern "C" {
  * solver's inner iteration does (FP16/BF16: per-site scaled). */
 #define STAG_ROUND_OUTPUT 0x100
 
+/* OR-ed into the precision of stag_cg_solve / stag_time_dslash with STAG_FP16
+ * or STAG_BF16: also store the Krylov vectors (p, A p and the intermediate
+ * D_oe p) at that precision with a per-site scale.  Without it only the links
+ * are stored at FP16/BF16 and the Krylov vectors stay FP32. */
+#define STAG_HALF_VECTORS 0x200
+
 /* context flags */
 #define STAG_ANTIPERIODIC_T 1 /* antiperiodic boundary in t (the sign b_mu above) */
 #define STAG_RECON12 2 /* reduced-precision links keep rows 0,1; row 2 = conj(row0 x row1) */
@@ -117,7 +123,9 @@ int stag_mdagm(stag_ctx *ctx, int precision, double mass, const double *in_even,
  * masses[] (Sec. 3: the mixed-precision CG inverter).  nrhs * nmass systems;
  * system (r, k) has source src[r], mass masses[k] and solution x[r * nmass + k].
  *   precision  STAG_FP64: plain FP64 CG.  STAG_FP32/FP16/BF16: the inner
- *              iteration runs at that storage precision (FP32 arithmetic), the
+ *              iteration runs with links stored at that precision (FP32
+ *              arithmetic; Krylov vectors FP32, or FP16/BF16 per-site scaled
+ *              with STAG_HALF_VECTORS), the
  *              solution is accumulated and the residual recomputed in FP64
  *              whenever the iterated residual has dropped by 10x since the last
  *              recomputation ("reliable update"), and at convergence.

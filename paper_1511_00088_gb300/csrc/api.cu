@@ -109,7 +109,8 @@ struct PinnedBuf {
 // solver workspace for one (number of systems, precision, link format)
 struct Work {
   int nsys = 0, prec = -1, recon = -1;
-  int RP = P32;
+  int VP = P32;  // precision of the Krylov vectors p, Ap, t
+  int RP = P32;  // precision of the iterated residual r and partial solution x_lo
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
   int nbx_ds = 0, nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, Ap, t;
@@ -194,6 +195,19 @@ int arg_err(stag_ctx *c, const char *msg) {
 
 int valid_prec(int p) { return p == P64 || p == P32 || p == P16 || p == PBF; }
 
+// Solver precision argument: link storage in the low byte; STAG_HALF_VECTORS
+// also stores the Krylov vectors at FP16/BF16 (per-site scaled).
+bool solver_precs(int precision, int *LP, int *VP, int *RP) {
+  const int P = precision & 0xff;
+  const bool hv = (precision & STAG_HALF_VECTORS) != 0;
+  if (!valid_prec(P) || (precision & ~(0xff | STAG_HALF_VECTORS))) return false;
+  if (hv && !(P == P16 || P == PBF)) return false;
+  *LP = P;
+  *VP = (P == P64) ? P64 : (hv ? P : P32);
+  *RP = (P == P64) ? P64 : P32;
+  return true;
+}
+
 // device pointer to the FP64 ABI vector `src` (copied through `stage` when on the host)
 int vec_in(stag_ctx *c, const double *src, DevBuf &stage, size_t off_bytes, const double2 **out) {
   const size_t bytes = sizeof(double) * 6ull * c->Ve;
@@ -253,23 +267,26 @@ Ctl no_ctl() {
 // solver
 // ---------------------------------------------------------------------------
 
-int work_prepare(stag_ctx *c, int nsys, int prec) {
+int work_prepare(stag_ctx *c, int nsys, int precision) {
   Work &w = c->w;
+  int prec, VP, RP;
+  if (!solver_precs(precision, &prec, &VP, &RP)) return arg_err(c, "bad solver precision");
   const int recon = link_recon(c, prec);
-  if (w.nsys == nsys && w.prec == prec && w.recon == recon) return STAG_OK;
+  if (w.nsys == nsys && w.prec == prec && w.VP == VP && w.recon == recon) return STAG_OK;
   w.drop_graph();
   c->last_nsys = 0;
   w.nsys = nsys;
   w.prec = prec;
   w.recon = recon;
-  w.RP = (prec == P64) ? P64 : P32;
+  w.VP = VP;
+  w.RP = RP;
   if (prec == P64) w.NS = nsys >= 4 ? 4 : 1;
   else w.NS = nsys >= 8 ? 8 : nsys >= 4 ? 4 : 1;
   w.G = (nsys + w.NS - 1) / w.NS;
   w.NS64 = nsys >= 4 ? 4 : 1;
   w.G64 = (nsys + w.NS64 - 1) / w.NS64;
   const int Ve = c->Ve;
-  w.nbx_ds = (Ve + DS_BT - 1) / DS_BT;
+  w.nbx_ds = (Ve + DS_SITES - 1) / DS_SITES;
   w.nbx_bl = (Ve + BLAS_BT - 1) / BLAS_BT;
   w.pstride = w.nbx_ds > w.nbx_bl ? w.nbx_ds : w.nbx_bl;
   CK(w.b64.ensure(P64, nsys, Ve));
@@ -277,9 +294,9 @@ int work_prepare(stag_ctx *c, int nsys, int prec) {
   CK(w.t64.ensure(P64, nsys, Ve));
   CK(w.r.ensure(w.RP, nsys, Ve));
   CK(w.x.ensure(w.RP, nsys, Ve));
-  CK(w.p.ensure(prec, nsys, Ve));
-  CK(w.Ap.ensure(prec, nsys, Ve));
-  CK(w.t.ensure(prec, nsys, Ve));
+  CK(w.p.ensure(VP, nsys, Ve));
+  CK(w.Ap.ensure(VP, nsys, Ve));
+  CK(w.t.ensure(VP, nsys, Ve));
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
   CK(w.tickets.ensure(sizeof(unsigned) * (nsys + 1)));
@@ -350,19 +367,19 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.in = w.p.arg();
   a.out = w.t.arg();
   a.fin = FIN_NONE;
-  CK(launch_dslash(w.prec, w.recon, w.prec, w.prec, w.NS, EPI_PLAIN, w.nbx_ds * w.G, s, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.nbx_ds * w.G, s, a));
   // K2: Ap = 4 m^2 p - D_eo t, <p, Ap>
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.out = w.Ap.arg();
   a.fin = FIN_ALPHA;
-  CK(launch_dslash(w.prec, w.recon, w.prec, w.prec, w.NS, EPI_MDAGM_DOT, w.nbx_ds * w.G, s, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT, w.nbx_ds * w.G, s, a));
   // K3: r -= alpha Ap, x += alpha p, ||r||^2
   BlasArgs b = blas_base(c, ctl);
   b.gate = GATE_RUNNING;
   b.fin = FIN_NORM;
-  CK(launch_axpy_norm(w.prec, w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  CK(launch_axpy_norm(w.VP, w.RP, w.NS, w.nbx_bl * w.G, s, b));
   return STAG_OK;
 }
 
@@ -400,7 +417,7 @@ int enqueue_xpay(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   BlasArgs b = blas_base(c, ctl);
   b.gate = GATE_RUNNING;
   b.fin = FIN_NONE;
-  CK(launch_xpay(w.prec, w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  CK(launch_xpay(w.VP, w.RP, w.NS, w.nbx_bl * w.G, s, b));
   return STAG_OK;
 }
 
@@ -484,7 +501,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
   CKS(work_prepare(c, nsys, prec));
   Work &w = c->w;
   const void *lo = nullptr;
-  CKS(links_for(c, prec, &lo));
+  CKS(links_for(c, w.prec, &lo));
 
   // sources -> b64 (FP64 internal layout)
   for (int r = 0; r < nrhs; ++r) {
@@ -500,7 +517,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     const double m = masses[j % nmass];
     hs[j].m4 = 4.0 * m * m;
     hs[j].tol = tol;
-    hs[j].delta = (prec == P64) ? 0.0 : 0.1;
+    hs[j].delta = (w.prec == P64) ? 0.0 : 0.1;
     hs[j].maxiter = maxiter;
   }
   CK(cudaMemcpyAsync(w.st.p, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, c->stream));
@@ -509,7 +526,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     BlasArgs b = blas_base(c, ctl0);
     b.gate = GATE_NONE;
     b.fin = FIN_INIT;
-    CK(launch_cg_init(prec, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
+    CK(launch_cg_init(w.VP, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
   }
 
   bool ran = false;
@@ -594,7 +611,7 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
   a.gate = GATE_NONE;
   a.fin = FIN_NONE;
   a.m4_single = 4.0 * mass * mass;
-  const int nb = (Ve + DS_BT - 1) / DS_BT;
+  const int nb = (Ve + DS_SITES - 1) / DS_SITES;
   if (which == 0 || which == 1) {  // 0: D_oe (out odd), 1: D_eo (out even)
     a.par_out = which == 0 ? 1 : 0;
     a.in = c->api_a.arg();
@@ -765,7 +782,11 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
   if ((long long)nrhs * nmass > 4096) return arg_err(c, "at most 4096 systems per solve");
   if (!(tol > 0.0) || !(tol < 1.0)) return arg_err(c, "tol must be in (0, 1)");
   if (maxiter < 1) return arg_err(c, "maxiter must be >= 1");
-  if (!valid_prec(precision)) return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16");
+  {
+    int a_, b_, c_;
+    if (!solver_precs(precision, &a_, &b_, &c_))
+      return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16 (FP16/BF16 optionally | STAG_HALF_VECTORS)");
+  }
   for (int r = 0; r < nrhs; ++r)
     if (!src[r]) return arg_err(c, "NULL source");
   for (int j = 0; j < nrhs * nmass; ++j)
@@ -788,13 +809,15 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
 int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_launch,
                      double *bytes_per_launch) {
   if (!c) return STAG_ERR_ARG;
-  if (!valid_prec(precision) || nlaunch < 1 || !ms_per_launch) return arg_err(c, "bad argument");
+  int LP_, VP_, RP_;
+  if (!solver_precs(precision, &LP_, &VP_, &RP_) || nlaunch < 1 || !ms_per_launch)
+    return arg_err(c, "bad argument");
   CK(cudaSetDevice(c->device));
-  const int nsys = c->w.nsys > 0 && c->w.prec == precision ? c->w.nsys : 1;
+  const int nsys = c->w.nsys > 0 && c->w.prec == LP_ && c->w.VP == VP_ ? c->w.nsys : 1;
   CKS(work_prepare(c, nsys, precision));
   Work &w = c->w;
   const void *lo = nullptr;
-  CKS(links_for(c, precision, &lo));
+  CKS(links_for(c, w.prec, &lo));
   DsArgs a = ds_base(c);
   a.links = lo;
   a.nsys = w.nsys;
@@ -809,10 +832,10 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(precision, w.recon, precision, precision, w.NS, EPI_PLAIN, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(precision, w.recon, precision, precision, w.NS, EPI_PLAIN, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -821,8 +844,8 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   cudaEventDestroy(e1);
   *ms_per_launch = (double)ms / nlaunch;
   if (bytes_per_launch) {
-    const double lb = (double)cplx_bytes(precision) * (w.recon ? 6 : 9);
-    const double vb = (double)cplx_bytes(precision) * 3 + ((precision == P16 || precision == PBF) ? 4 : 0);
+    const double lb = (double)cplx_bytes(w.prec) * (w.recon ? 6 : 9);
+    const double vb = (double)cplx_bytes(w.VP) * 3 + ((w.VP == P16 || w.VP == PBF) ? 4 : 0);
     *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * 2.0 * vb);
   }
   return STAG_OK;

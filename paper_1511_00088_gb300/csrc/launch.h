@@ -7,6 +7,7 @@
 namespace stag {
 
 constexpr int DS_BT = 128;    // threads per block of the half-operator kernels
+constexpr int DS_SITES = DS_BT / LANES_PER_SITE;  // output sites per half-operator block
 constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
 
 // Launch k_dslash<LP, recon, VP, OP, NS, EPI> on `nblocks` blocks.  Returns

@@ -203,6 +203,34 @@ __device__ __forceinline__ void store_vec(const VecArg &f, int k, int s, int Ve,
   }
 }
 
+// Store the share of one site written by lane c of its four lanes: colour c
+// (c < 3); for FP16/BF16 lane 3 writes the per-site scale.  Every lane holds
+// the whole site, so the scale (max over the 6 components) is computed locally
+// and the codes equal those of store_vec.
+template <int P, class R>
+__device__ __forceinline__ void store_colour(const VecArg &f, int k, int s, int Ve, int c, const R (&v)[6]) {
+  typedef typename Tr<P>::S2 S2;
+  typedef typename Tr<P>::R SR;
+  S2 *p = reinterpret_cast<S2 *>(f.v) + (long long)k * f.sstr + s;
+  if (Tr<P>::scaled) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) m = fmaxf(m, fabsf((float)v[i]));
+    if (c < 3) {
+      float qr = 0.f, qi = 0.f;
+      if (m > 0.f) {
+        qr = __fdiv_rn((float)v[2 * c], m);
+        qi = __fdiv_rn((float)v[2 * c + 1], m);
+      }
+      p[(long long)c * Ve] = from_r<P>((SR)qr, (SR)qi);
+    } else {
+      f.scale[(long long)k * Ve + s] = m;
+    }
+  } else if (c < 3) {
+    p[(long long)c * Ve] = from_r<P>((SR)v[2 * c], (SR)v[2 * c + 1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // links
 // ---------------------------------------------------------------------------
@@ -409,7 +437,16 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
     double s = 0.0;
     if (j0 + k < nsys) {
       const double *p = c.partials + ((long long)(j0 + k) * NVMAX + v) * c.pstride;
-      for (int i = lane; i < nbx; i += 32) s += __ldcg(p + i);
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int i = lane;
+      for (; i + 96 < nbx; i += 128) {
+        s0 += __ldcg(p + i);
+        s1 += __ldcg(p + i + 32);
+        s2 += __ldcg(p + i + 64);
+        s3 += __ldcg(p + i + 96);
+      }
+      for (; i < nbx; i += 32) s0 += __ldcg(p + i);
+      s = (s0 + s1) + (s2 + s3);
     }
     s = warp_sum(s);
     if (lane == 0) sums[k][v] = s;
@@ -455,11 +492,21 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
 // ---------------------------------------------------------------------------
 // the half operator with fused epilogues
 // ---------------------------------------------------------------------------
+// Thread mapping: four consecutive lanes own one output site, lane mu = 0..3
+// applies both hops of direction mu (2 links, 2 neighbour vectors, loaded
+// together: one memory round trip per thread instead of eight).  A butterfly
+// over the four lanes sums the directions, so every lane ends with the whole
+// site; lane c < 3 then writes colour c (lane 3 the FP16/BF16 scale).  A warp
+// covers 8 sites; per link element it reads 4 runs of 8 consecutive complex
+// numbers (full 32-byte sectors).
+//
 // EPI_PLAIN:     out = D in
 // EPI_MDAGM:     out = m4 center - D in
 // EPI_MDAGM_DOT: as EPI_MDAGM, plus sum_s Re<center, out> per system -> FIN_ALPHA
-// EPI_RESID:     (FP64) out = b - (m4 x - D in), reduced to the output storage,
-//                plus ||b - A x||^2 per system (in FP64) -> FIN_RESID
+// EPI_RESID:     (FP64) out = b - (m4 x - D in), stored at the output precision,
+//                plus ||b - A x||^2 per system (FP64) -> FIN_RESID
+constexpr int LANES_PER_SITE = 4;
+
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
@@ -468,104 +515,100 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   const int G = a.ngroups;
   const int grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
   const int j0 = grp * NS;
+  const int mu = threadIdx.x & 3;
+  const int s = bx * (BT / LANES_PER_SITE) + (threadIdx.x >> 2);
+  const bool valid = s < Ve;
   bool act[NS];
   R m4[NS];
+  bool any = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     act[k] = sys_gate(a.ctl, a.gate, j0 + k, a.nsys);
+    any |= act[k];
     m4[k] = (R)((a.ctl.st != nullptr && j0 + k < a.nsys) ? a.ctl.st[j0 + k].m4 : a.m4_single);
   }
   double part[NS][1];
 #pragma unroll
   for (int k = 0; k < NS; ++k) part[k][0] = 0.0;
 
-  bool any = false;
+  R acc[NS][6];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) any |= act[k];
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[k][i] = 0;
 
-  const int s = bx * BT + threadIdx.x;
-  if (any && s < Ve) {
-    const int P = a.par_out;
+  const int P = a.par_out;
+  if (any && valid) {
     int x[4];
     site_coords(g, P, s, x);
-    R acc[NS][6];
+    const int Lmu = mu == 0 ? g.L0 : mu == 1 ? g.L1 : mu == 2 ? g.L2 : g.L3;
+    int eb = 0;  // x_0 + ... + x_{mu-1}
+    if (mu > 0) eb += x[0];
+    if (mu > 1) eb += x[1];
+    if (mu > 2) eb += x[2];
+    const R eta = (eb & 1) ? R(-1) : R(1);
+    const int xm = x[mu];
+    int xf[4] = {x[0], x[1], x[2], x[3]};
+    int xb[4] = {x[0], x[1], x[2], x[3]};
+    xf[mu] = (xm + 1 == Lmu) ? 0 : xm + 1;
+    xb[mu] = (xm == 0) ? Lmu - 1 : xm - 1;
+    const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
+    const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
+    R bf = eta, bb = eta;
+    if (mu == 3 && g.ap) {
+      if (xm == g.L3 - 1) bf = -bf;
+      if (xm == 0) bb = -bb;
+    }
+    R uf[18], ub[18];
+    load_link<LP, RECON>(a.links, Ve, P, mu, s, uf);
+    load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, ub);
 #pragma unroll
-    for (int k = 0; k < NS; ++k)
+    for (int k = 0; k < NS; ++k) {
+      if (!act[k]) continue;
+      R vf[6], vb[6];
+      load_vec<VP>(a.in, k + j0, sf, Ve, vf);
+      load_vec<VP>(a.in, k + j0, sb, Ve, vb);
+      mv_acc(uf, vf, bf, acc[k]);
+      mvdag_acc(ub, vb, -bb, acc[k]);
+    }
+  }
+  // sum the four directions: every lane of the site ends with the total
 #pragma unroll
-      for (int i = 0; i < 6; ++i) acc[k][i] = 0;
-
-    const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
-    int eta_bits = 0;  // running sum x_0 + ... + x_{mu-1}
+  for (int k = 0; k < NS; ++k)
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const R eta = (eta_bits & 1) ? R(-1) : R(1);
-      eta_bits += x[mu];
-      int xf[4] = {x[0], x[1], x[2], x[3]};
-      int xb[4] = {x[0], x[1], x[2], x[3]};
-      xf[mu] = (x[mu] + 1 == Ls[mu]) ? 0 : x[mu] + 1;
-      xb[mu] = (x[mu] == 0) ? Ls[mu] - 1 : x[mu] - 1;
-      const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
-      const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
-      R bf = eta, bb = eta;
-      if (mu == 3 && g.ap) {
-        if (x[3] == g.L3 - 1) bf = -bf;
-        if (x[3] == 0) bb = -bb;
-      }
-      {
-        R u[18];
-        load_link<LP, RECON>(a.links, Ve, P, mu, s, u);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          if (!act[k]) continue;
-          R v[6];
-          load_vec<VP>(a.in, k + j0, sf, Ve, v);
-          mv_acc(u, v, bf, acc[k]);
-        }
-      }
-      {
-        R u[18];
-        load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, u);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          if (!act[k]) continue;
-          R v[6];
-          load_vec<VP>(a.in, k + j0, sb, Ve, v);
-          mvdag_acc(u, v, -bb, acc[k]);
-        }
-      }
+    for (int i = 0; i < 6; ++i) {
+      acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], 1);
+      acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], 2);
     }
 
+  if (any && valid) {
+    const int c = mu;  // colour written by this lane (lane 3: the scale)
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (!act[k]) continue;
       const int j = k + j0;
+      R o[6];
       if (EPI == EPI_PLAIN) {
-        store_vec<OP>(a.out, j, s, Ve, acc[k]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) o[i] = acc[k][i];
       } else if (EPI == EPI_MDAGM || EPI == EPI_MDAGM_DOT) {
-        R c[6], o[6];
-        load_vec<VP>(a.center, j, s, Ve, c);
+        R cv[6];
+        load_vec<VP>(a.center, j, s, Ve, cv);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) o[i] = m4[k] * c[i] - acc[k][i];
-        store_vec<OP>(a.out, j, s, Ve, o);
-        if (EPI == EPI_MDAGM_DOT) {
-          R d = 0;
-#pragma unroll
-          for (int i = 0; i < 6; ++i) d += c[i] * o[i];
+        for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
+        if (EPI == EPI_MDAGM_DOT && c < 3) {
+          const R d = cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
           part[k][0] += (double)d;
         }
       } else {  // EPI_RESID (R = double)
-        R xx[6], bv[6], o[6];
+        R xx[6], bv[6];
         load_vec<P64>(a.center, j, s, Ve, xx);
         load_vec<P64>(a.aux, j, s, Ve, bv);
-        double nn = 0.0;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
-          nn += (double)o[i] * (double)o[i];
-        }
-        store_vec<OP>(a.out, j, s, Ve, o);
-        part[k][0] += nn;
+        for (int i = 0; i < 6; ++i) o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
+        if (c < 3) part[k][0] += (double)o[2 * c] * (double)o[2 * c] + (double)o[2 * c + 1] * (double)o[2 * c + 1];
       }
+      store_colour<OP>(a.out, j, s, Ve, c, o);
     }
   }
 

@@ -29,6 +29,7 @@ STAG_ERR_STATE = -7
 
 STAG_FP64, STAG_FP32, STAG_FP16, STAG_BF16 = 0, 1, 2, 3
 STAG_ROUND_OUTPUT = 0x100
+STAG_HALF_VECTORS = 0x200
 STAG_ANTIPERIODIC_T = 1
 STAG_RECON12 = 2
 

@@ -16,7 +16,8 @@ from paper_1511_00088_gb300 import stag, synth
 
 pytestmark = pytest.mark.gpu
 
-PREC = {"fp64": stag.STAG_FP64, "fp32": stag.STAG_FP32, "fp16": stag.STAG_FP16, "bf16": stag.STAG_BF16}
+PREC = {"fp64": stag.STAG_FP64, "fp32": stag.STAG_FP32, "fp16": stag.STAG_FP16, "bf16": stag.STAG_BF16,
+        "fp16hv": stag.STAG_FP16 | stag.STAG_HALF_VECTORS, "bf16hv": stag.STAG_BF16 | stag.STAG_HALF_VECTORS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,7 +35,7 @@ def check_solution(L, U, m, b, x, tr_gpu, tol=1e-10):
     return tr
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16", "fp16hv", "bf16hv"])
 def test_config0_8x4(prec):
     """8^4, links exp(0.3 i H), m = 0.05, one Gaussian source, tol 1e-10."""
     L = (8, 8, 8, 8)
@@ -55,7 +56,7 @@ def test_config0_8x4(prec):
     assert it[0] <= 3 * it_o + 20, (it[0], it_o)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16hv"])
 @pytest.mark.parametrize("L", [(4, 2, 6, 8), (6, 6, 6, 12), (2, 2, 2, 2)])
 def test_odd_shapes_device_buffers(prec, L):
     V = synth.volume(L)
@@ -70,7 +71,7 @@ def test_odd_shapes_device_buffers(prec, L):
     check_solution(L, U, m, b, xs[0].cpu().numpy(), tr[0])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16hv"])
 def test_multi_rhs_multi_mass(prec):
     """3 sources x 3 masses in one solve: every system to 1e-10 (per-system
     alpha, beta, reliable updates and convergence masks)."""
@@ -165,7 +166,7 @@ def test_deterministic_and_graph_equals_eager():
     assert np.array_equal(x1[0], x3[0]) and it1[0] == it3[0]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16", "bf16"])
 def test_config1_production_lattice(prec):
     """20^3 x 64, links exp(0.4 i H), m = 0.01: the benchmark's workload."""
     L = (20, 20, 20, 64)
