@@ -71,7 +71,7 @@ def test_odd_shapes_device_buffers(prec, L):
     check_solution(L, U, m, b, xs[0].cpu().numpy(), tr[0])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16hv"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16", "fp16hv"])
 def test_multi_rhs_multi_mass(prec):
     """3 sources x 3 masses in one solve: every system to 1e-10 (per-system
     alpha, beta, reliable updates and convergence masks)."""
