@@ -24,7 +24,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "launch.h"
@@ -112,9 +115,10 @@ struct Work {
   int VP = P32;  // precision of the Krylov vectors p, Ap, t
   int RP = P32;  // precision of the iterated residual r and partial solution x_lo
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
-  int nbx_ds = 0, nbx_bl = 0, pstride = 0;
+  int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
+  int nbx_bl = 0, pstride = 0, cstride = 0;
   VecBuf b64, x64, t64, r, x, p, Ap, t;
-  DevBuf st, partials, tickets, flags;
+  DevBuf st, partials, partials2, tickets, flags;
   PinnedBuf h_st, h_flags;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -264,6 +268,108 @@ Ctl no_ctl() {
 }
 
 // ---------------------------------------------------------------------------
+// autotuner: lanes per output site of the half operator
+// ---------------------------------------------------------------------------
+// The choice (1 or 2 lanes per site) is made per (link precision, reconstruct,
+// vector precision, systems per thread, system groups, lattice) by timing both
+// candidates with CUDA events (3 warm-up and 10 timed launches of the plain
+// operator on the caller's buffers) and is cached for the process.  STAG_LANES
+// = 1 or 2 forces a value; STAG_TUNE_CACHE names a text file that persists the
+// cache ("key lanes" lines) across processes.
+typedef std::tuple<int, int, int, int, int, int, int, int, int> TuneKey;
+std::map<TuneKey, int> g_tune;
+std::mutex g_tune_mu;
+bool g_tune_loaded = false;
+
+std::string tune_key_str(const TuneKey &k) {
+  char b[160];
+  snprintf(b, sizeof b, "%d_%d_%d_%d_%d_%dx%dx%dx%d", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+           std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), std::get<8>(k));
+  return b;
+}
+
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("STAG_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  int v[9], lanes;
+  while (fscanf(f, "%d_%d_%d_%d_%d_%dx%dx%dx%d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                &v[8], &lanes) == 10)
+    g_tune[TuneKey(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8])] = lanes;
+  fclose(f);
+}
+
+void tune_cache_store(const TuneKey &k, int lanes) {
+  const char *path = getenv("STAG_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d\n", tune_key_str(k).c_str(), lanes);
+  fclose(f);
+}
+
+int tune_lanes(stag_ctx *c, int LP, int recon, int VP, int NS, int G, int nsys, const void *links, VecArg in,
+               VecArg out, int *lanes_out) {
+  const char *force = getenv("STAG_LANES");
+  if (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) {
+    *lanes_out = force[0] - '0';
+    return STAG_OK;
+  }
+  const TuneKey key(LP, recon, VP, NS, G, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *lanes_out = it->second;
+      return STAG_OK;
+    }
+  }
+  DsArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = c->g;
+  a.links = links;
+  a.in = in;
+  a.out = out;
+  a.nsys = nsys;
+  a.ngroups = G;
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.par_out = 1;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_l = 1;
+  for (int l = 1; l <= 2; ++l) {
+    const int nb = ds_blocks(c->Ve, l) * G;
+    for (int i = 0; i < 3; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI_PLAIN, l, nb, c->stream, a));
+    CK(cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < 10; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI_PLAIN, l, nb, c->stream, a));
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_l = l;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_l;
+    tune_cache_store(key, best_l);
+  }
+  *lanes_out = best_l;
+  return STAG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // solver
 // ---------------------------------------------------------------------------
 
@@ -286,9 +392,10 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   w.NS64 = nsys >= 4 ? 4 : 1;
   w.G64 = (nsys + w.NS64 - 1) / w.NS64;
   const int Ve = c->Ve;
-  w.nbx_ds = (Ve + DS_SITES - 1) / DS_SITES;
+  const int nbx_ds_max = ds_blocks(Ve, 2);
   w.nbx_bl = (Ve + BLAS_BT - 1) / BLAS_BT;
-  w.pstride = w.nbx_ds > w.nbx_bl ? w.nbx_ds : w.nbx_bl;
+  w.pstride = nbx_ds_max > w.nbx_bl ? nbx_ds_max : w.nbx_bl;
+  w.cstride = (w.pstride + RED_CHUNK - 1) / RED_CHUNK;
   CK(w.b64.ensure(P64, nsys, Ve));
   CK(w.x64.ensure(P64, nsys, Ve));
   CK(w.t64.ensure(P64, nsys, Ve));
@@ -299,15 +406,23 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.t.ensure(VP, nsys, Ve));
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
-  CK(w.tickets.ensure(sizeof(unsigned) * (nsys + 1)));
+  CK(w.partials2.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.cstride));
+  const size_t ntickets = (size_t)nsys + 1 + (size_t)nsys * w.cstride;
+  CK(w.tickets.ensure(sizeof(unsigned) * ntickets));
   CK(w.flags.ensure(sizeof(int) * 2));
   CK(w.h_st.ensure(sizeof(SysState) * nsys));
   CK(w.h_flags.ensure(sizeof(int) * 2));
-  CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * (nsys + 1), c->stream));
+  CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * ntickets, c->stream));
   CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
   // defined contents for the timing entry point before any solve
   CK(cudaMemsetAsync(w.p.data.p, 0, w.p.data.n, c->stream));
   if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
+  CK(cudaMemsetAsync(w.x64.data.p, 0, w.x64.data.n, c->stream));
+  // pick the thread mapping of the inner and the FP64 half operators
+  const void *lo = nullptr;
+  CKS(links_for(c, prec, &lo));
+  CKS(tune_lanes(c, prec, recon, VP, w.NS, w.G, nsys, lo, w.p.arg(), w.t.arg(), &w.lanes));
+  CKS(tune_lanes(c, P64, 0, P64, w.NS64, w.G64, nsys, c->links64.p, w.x64.arg(), w.t64.arg(), &w.lanes64));
   return STAG_OK;
 }
 
@@ -317,10 +432,13 @@ Ctl work_ctl(stag_ctx *c, bool graph) {
   memset(&k, 0, sizeof k);
   k.st = (SysState *)w.st.p;
   k.partials = (double *)w.partials.p;
+  k.partials2 = (double *)w.partials2.p;
   k.grp_ticket = (unsigned *)w.tickets.p;
   k.all_ticket = (unsigned *)w.tickets.p + w.nsys;
+  k.chunk_ticket = (unsigned *)w.tickets.p + w.nsys + 1;
   k.flags = (int *)w.flags.p;
   k.pstride = w.pstride;
+  k.cstride = w.cstride;
   k.use_graph_cond = graph ? 1 : 0;
   k.h_loop = w.h_loop;
   k.h_update = w.h_update;
@@ -367,14 +485,15 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.in = w.p.arg();
   a.out = w.t.arg();
   a.fin = FIN_NONE;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.nbx_ds * w.G, s, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
   // K2: Ap = 4 m^2 p - D_eo t, <p, Ap>
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.out = w.Ap.arg();
   a.fin = FIN_ALPHA;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT, w.nbx_ds * w.G, s, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s,
+                   a));
   // K3: r -= alpha Ap, x += alpha p, ||r||^2
   BlasArgs b = blas_base(c, ctl);
   b.gate = GATE_RUNNING;
@@ -400,14 +519,14 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.in = w.x64.arg();
   a.out = w.t64.arg();
   a.fin = FIN_NONE;
-  CK(launch_dslash(P64, 0, P64, P64, w.NS64, EPI_PLAIN, w.nbx_ds * w.G64, s, a));
+  CK(launch_dslash(P64, 0, P64, P64, w.NS64, EPI_PLAIN, w.lanes64, ds_blocks(c->Ve, w.lanes64) * w.G64, s, a));
   a.par_out = 0;
   a.in = w.t64.arg();
   a.center = w.x64.arg();
   a.aux = w.b64.arg();
   a.out = w.r.arg();
   a.fin = FIN_RESID;
-  CK(launch_dslash(P64, 0, P64, w.RP, w.NS64, EPI_RESID, w.nbx_ds * w.G64, s, a));
+  CK(launch_dslash(P64, 0, P64, w.RP, w.NS64, EPI_RESID, w.lanes64, ds_blocks(c->Ve, w.lanes64) * w.G64, s, a));
   return STAG_OK;
 }
 
@@ -611,23 +730,25 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
   a.gate = GATE_NONE;
   a.fin = FIN_NONE;
   a.m4_single = 4.0 * mass * mass;
-  const int nb = (Ve + DS_SITES - 1) / DS_SITES;
+  int lanes = 1;
+  CKS(tune_lanes(c, P, recon, VP, 1, 1, 1, links, c->api_a.arg(), c->api_b.arg(), &lanes));
+  const int nb = ds_blocks(Ve, lanes);
   if (which == 0 || which == 1) {  // 0: D_oe (out odd), 1: D_eo (out even)
     a.par_out = which == 0 ? 1 : 0;
     a.in = c->api_a.arg();
     a.out = c->api_b.arg();
-    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, nb, c->stream, a));
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, lanes, nb, c->stream, a));
   } else {  // M^dag M
     a.par_out = 1;
     a.in = c->api_a.arg();
     a.out = c->api_c.arg();
     CK(c->api_c.ensure(VP, 1, Ve));
-    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, nb, c->stream, a));
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_PLAIN, lanes, nb, c->stream, a));
     a.par_out = 0;
     a.in = c->api_c.arg();
     a.center = c->api_a.arg();
     a.out = c->api_b.arg();
-    CK(launch_dslash(P, recon, VP, VP, 1, EPI_MDAGM, nb, c->stream, a));
+    CK(launch_dslash(P, recon, VP, VP, 1, EPI_MDAGM, lanes, nb, c->stream, a));
   }
   CKS(vec_out(c, c->api_b, 0, out));
   CK(cudaStreamSynchronize(c->stream));
@@ -697,6 +818,9 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   c->g.Lxh = dims[0] / 2;
   c->g.Ve = c->Ve;
   c->g.ap = (flags & STAG_ANTIPERIODIC_T) ? 1 : 0;
+  c->g.dLxh = make_fastdiv((unsigned)(dims[0] / 2));
+  c->g.dL1 = make_fastdiv((unsigned)dims[1]);
+  c->g.dL2 = make_fastdiv((unsigned)dims[2]);
   const char *eager = getenv("STAG_EAGER");
   c->use_graph = !(eager && eager[0] == '1');
   cudaError_t e = cudaGetDevice(&c->device);
@@ -828,14 +952,14 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   a.par_out = 1;
   a.in = w.p.arg();
   a.out = w.t.arg();
-  const int nb = w.nbx_ds * w.G;
+  const int nb = ds_blocks(c->Ve, w.lanes) * w.G;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;

@@ -4,13 +4,13 @@
 
 namespace stag {
 
-cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                           cudaStream_t st, const DsArgs &a) {
   switch (LP) {
-    case P64: return launch_dslash_p64(recon, VP, OP, NS, EPI, nblocks, st, a);
-    case P32: return launch_dslash_p32(recon, VP, OP, NS, EPI, nblocks, st, a);
-    case P16: return launch_dslash_p16(recon, VP, OP, NS, EPI, nblocks, st, a);
-    case PBF: return launch_dslash_pbf(recon, VP, OP, NS, EPI, nblocks, st, a);
+    case P64: return launch_dslash_p64(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
+    case P32: return launch_dslash_p32(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
+    case P16: return launch_dslash_p16(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
+    case PBF: return launch_dslash_pbf(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
   }
   return cudaErrorNotSupported;
 }

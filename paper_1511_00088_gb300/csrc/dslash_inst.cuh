@@ -5,7 +5,10 @@
 
 #define STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_)                                      \
   if (recon == RC_ && VP == VP_ && OP == OP_ && NS == NS_ && EPI == EPI_) {              \
-    k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT><<<nblocks, DS_BT, 0, st>>>(a);         \
+    if (lanes == 2)                                                                      \
+      k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2><<<nblocks, DS_BT, 0, st>>>(a);    \
+    else                                                                                 \
+      k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1><<<nblocks, DS_BT, 0, st>>>(a);    \
     return cudaGetLastError();                                                           \
   }
 

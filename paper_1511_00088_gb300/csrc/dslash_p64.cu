@@ -1,7 +1,7 @@
 // FP64 instantiations of the half operator: the FP64 CG and the reliable update.
 #include "dslash_inst.cuh"
 namespace stag {
-cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a) {
   STAG_DS_EPIS(P64, 0, P64, P64, 1)
   STAG_DS_EPIS(P64, 0, P64, P64, 4)

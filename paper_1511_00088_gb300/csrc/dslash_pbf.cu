@@ -3,7 +3,7 @@
 // with a per-site scale (STAG_HALF_VECTORS, STAG_ROUND_OUTPUT).
 #include "dslash_inst.cuh"
 namespace stag {
-cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a) {
   STAG_DS_EPIS(PBF, 0, P32, P32, 1)
   STAG_DS_EPIS(PBF, 0, P32, P32, 4)

@@ -7,20 +7,26 @@
 namespace stag {
 
 constexpr int DS_BT = 128;    // threads per block of the half-operator kernels
-constexpr int DS_SITES = DS_BT / LANES_PER_SITE;  // output sites per half-operator block
+
+// blocks of the half operator for Ve sites with `lanes` lanes per site
+inline int ds_blocks(int Ve, int lanes) {
+  const int sites = DS_BT / lanes;
+  return (Ve + sites - 1) / sites;
+}
 constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
 
-// Launch k_dslash<LP, recon, VP, OP, NS, EPI> on `nblocks` blocks.  Returns
+// Launch k_dslash<LP, recon, VP, OP, NS, EPI, DS_BT, lanes> on `nblocks`
+// blocks (lanes = 1 or 2 lanes per output site).  Returns
 // cudaErrorNotSupported for a combination the library does not instantiate.
-cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                           cudaStream_t st, const DsArgs &a);
-cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a);
-cudaError_t launch_dslash_p32(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_p32(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a);
-cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a);
-cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int nblocks,
+cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a);
 
 cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);

@@ -36,11 +36,36 @@ template <> struct Tr<PBF> { typedef float R; typedef __nv_bfloat162 S2; static 
 // ---------------------------------------------------------------------------
 // plain-old-data argument blocks (passed by value to kernels)
 // ---------------------------------------------------------------------------
+// Division by a run-time invariant divisor with one multiply-high and shifts
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l,1))) >> max(l-1,0) with t = umulhi(m, n); exact
+// for every 32-bit n.  Built on the host by make_fastdiv().
+struct FastDiv {
+  unsigned m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  f.s1 = l ? 1u : 0u;
+  f.s2 = l ? l - 1 : 0u;
+  return f;
+}
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv &f) {
+  const unsigned t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Geom {
   int L0, L1, L2, L3;  // Lx, Ly, Lz, Lt
   int Lxh;             // Lx / 2
   int Ve;              // sites per parity
   int ap;              // antiperiodic time boundary
+  FastDiv dLxh, dL1, dL2;  // division by Lx/2, Ly, Lz
 };
 
 struct VecArg {
@@ -70,11 +95,14 @@ struct SysState {
 
 struct Ctl {
   SysState *st;          // [nsys]
-  double *partials;      // [nsys][NVMAX][pstride]
+  double *partials;      // [nsys][NVMAX][pstride]   one per block
+  double *partials2;     // [nsys][NVMAX][cstride]   one per chunk of RED_CHUNK blocks
   unsigned *grp_ticket;  // [ngroups]
+  unsigned *chunk_ticket;  // [ngroups][cstride]
   unsigned *all_ticket;  // [1]
   int *flags;            // [0] any system running, [1] any reliable update due
   int pstride;           // partial slots per (system, value)
+  int cstride;           // chunk slots per (system, value) = ceil(pstride / RED_CHUNK)
   int use_graph_cond;    // call cudaGraphSetConditional on the handles below
   cudaGraphConditionalHandle h_loop, h_update;
 };
@@ -203,12 +231,13 @@ __device__ __forceinline__ void store_vec(const VecArg &f, int k, int s, int Ve,
   }
 }
 
-// Store the share of one site written by lane c of its four lanes: colour c
-// (c < 3); for FP16/BF16 lane 3 writes the per-site scale.  Every lane holds
-// the whole site, so the scale (max over the 6 components) is computed locally
-// and the codes equal those of store_vec.
-template <int P, class R>
-__device__ __forceinline__ void store_colour(const VecArg &f, int k, int s, int Ve, int c, const R (&v)[6]) {
+// Store the share of one site written by `lane` of its LANES lanes: colours
+// c with c % LANES == lane; for FP16/BF16 the last lane also writes the
+// per-site scale.  Every lane holds the whole site, so the scale (max over the
+// 6 components) is computed locally and the codes equal those of store_vec.
+template <int P, int LANES, class R>
+__device__ __forceinline__ void store_site_share(const VecArg &f, int k, int s, int Ve, int lane,
+                                                 const R (&v)[6]) {
   typedef typename Tr<P>::S2 S2;
   typedef typename Tr<P>::R SR;
   S2 *p = reinterpret_cast<S2 *>(f.v) + (long long)k * f.sstr + s;
@@ -216,18 +245,21 @@ __device__ __forceinline__ void store_colour(const VecArg &f, int k, int s, int 
     float m = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) m = fmaxf(m, fabsf((float)v[i]));
-    if (c < 3) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c % LANES != lane) continue;
       float qr = 0.f, qi = 0.f;
       if (m > 0.f) {
         qr = __fdiv_rn((float)v[2 * c], m);
         qi = __fdiv_rn((float)v[2 * c + 1], m);
       }
       p[(long long)c * Ve] = from_r<P>((SR)qr, (SR)qi);
-    } else {
-      f.scale[(long long)k * Ve + s] = m;
     }
-  } else if (c < 3) {
-    p[(long long)c * Ve] = from_r<P>((SR)v[2 * c], (SR)v[2 * c + 1]);
+    if (lane == LANES - 1) f.scale[(long long)k * Ve + s] = m;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c % LANES == lane) p[(long long)c * Ve] = from_r<P>((SR)v[2 * c], (SR)v[2 * c + 1]);
   }
 }
 
@@ -299,12 +331,13 @@ __device__ __forceinline__ void mvdag_acc(const R (&u)[18], const R (&v)[6], R s
 // geometry
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void site_coords(const Geom &g, int par, int s, int (&x)[4]) {
-  const int xh = s % g.Lxh;
-  int r = s / g.Lxh;
-  x[1] = r % g.L1;
-  r /= g.L1;
-  x[2] = r % g.L2;
-  x[3] = r / g.L2;
+  const unsigned q1 = fast_div((unsigned)s, g.dLxh);  // y + Ly (z + Lz t)
+  const unsigned q2 = fast_div(q1, g.dL1);            // z + Lz t
+  const unsigned q3 = fast_div(q2, g.dL2);            // t
+  const int xh = s - (int)q1 * g.Lxh;
+  x[1] = (int)q1 - (int)q2 * g.L1;
+  x[2] = (int)q2 - (int)q3 * g.L2;
+  x[3] = (int)q3;
   x[0] = 2 * xh + ((par + x[1] + x[2] + x[3]) & 1);
 }
 
@@ -401,7 +434,14 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
 
 // Called by every thread of every block after it accumulated val[k][v] for
 // the NS systems j0 + k of its group.  bx/nbx: block index / count within the
-// group.  Deterministic: partials are summed in block order by fixed trees.
+// group.  Two-level and deterministic: each block publishes one partial per
+// (system, value); the last block to finish within a chunk of RED_CHUNK
+// consecutive blocks sums the chunk in block order; the last chunk to finish
+// sums the chunk sums in chunk order and runs the finalisers.  Fixed summation
+// trees throughout, so reruns are bit-identical; no serial tail longer than a
+// few loads per lane.
+constexpr int RED_CHUNK = 64;
+
 template <int NS, int NV>
 __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, double (&val)[NS][NV], int grp,
                                                     int ngroups, int j0, int nsys, int bx, int nbx) {
@@ -416,8 +456,11 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
       if (lane == 0) red[warp][k * NV + v] = w;
     }
   __syncthreads();
+  const int chunk = bx / RED_CHUNK;
+  const int nchunks = (nbx + RED_CHUNK - 1) / RED_CHUNK;
+  const int csize = min(RED_CHUNK, nbx - chunk * RED_CHUNK);
   if (threadIdx.x == 0) {
-    // one thread publishes the block's partials, then takes a ticket
+    // one thread publishes the block's partials, then takes a ticket of its chunk
     for (int kv = 0; kv < NS * NV; ++kv) {
       const int k = kv / NV, v = kv % NV;
       double s = 0.0;
@@ -425,28 +468,39 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
       if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = s;
     }
     __threadfence();
-    const unsigned t = atomicAdd(c.grp_ticket + grp, 1u);
-    am_last = (t == (unsigned)(nbx - 1));
+    const unsigned t = atomicAdd(c.chunk_ticket + (long long)grp * c.cstride + chunk, 1u);
+    am_last = (t == (unsigned)(csize - 1));
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
+  // level 1: this chunk's partials, in block order
+  for (int kv = warp; kv < NS * NV; kv += nwarp) {
+    const int k = kv / NV, v = kv % NV;
+    if (j0 + k >= nsys) continue;
+    const double *p = c.partials + ((long long)(j0 + k) * NVMAX + v) * c.pstride + chunk * RED_CHUNK;
+    double s = (lane < csize ? __ldcg(p + lane) : 0.0) + (lane + 32 < csize ? __ldcg(p + lane + 32) : 0.0);
+    s = warp_sum(s);
+    if (lane == 0) c.partials2[((long long)(j0 + k) * NVMAX + v) * c.cstride + chunk] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.chunk_ticket[(long long)grp * c.cstride + chunk] = 0u;
+    __threadfence();
+    const unsigned t = atomicAdd(c.grp_ticket + grp, 1u);
+    am_last = (t == (unsigned)(nchunks - 1));
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // level 2: the chunk sums, in chunk order
   __shared__ double sums[NS][NVMAX];
   for (int kv = warp; kv < NS * NV; kv += nwarp) {
     const int k = kv / NV, v = kv % NV;
     double s = 0.0;
     if (j0 + k < nsys) {
-      const double *p = c.partials + ((long long)(j0 + k) * NVMAX + v) * c.pstride;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int i = lane;
-      for (; i + 96 < nbx; i += 128) {
-        s0 += __ldcg(p + i);
-        s1 += __ldcg(p + i + 32);
-        s2 += __ldcg(p + i + 64);
-        s3 += __ldcg(p + i + 96);
-      }
-      for (; i < nbx; i += 32) s0 += __ldcg(p + i);
-      s = (s0 + s1) + (s2 + s3);
+      const double *p = c.partials2 + ((long long)(j0 + k) * NVMAX + v) * c.cstride;
+      for (int i = lane; i < nchunks; i += 32) s += __ldcg(p + i);
     }
     s = warp_sum(s);
     if (lane == 0) sums[k][v] = s;
@@ -492,31 +546,30 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
 // ---------------------------------------------------------------------------
 // the half operator with fused epilogues
 // ---------------------------------------------------------------------------
-// Thread mapping: four consecutive lanes own one output site, lane mu = 0..3
-// applies both hops of direction mu (2 links, 2 neighbour vectors, loaded
-// together: one memory round trip per thread instead of eight).  A butterfly
-// over the four lanes sums the directions, so every lane ends with the whole
-// site; lane c < 3 then writes colour c (lane 3 the FP16/BF16 scale).  A warp
-// covers 8 sites; per link element it reads 4 runs of 8 consecutive complex
-// numbers (full 32-byte sectors).
+// Thread mapping: LANES consecutive lanes own one output site (LANES = 1 or 2);
+// a lane handles 4 / LANES directions, and for each direction loads both links
+// and both neighbour vectors before using them, so a thread has at most four
+// dependent memory rounds (two with LANES = 2) and many loads in flight.  With
+// LANES = 2 a butterfly sums the two halves, then the lanes share the stores.
+// (Four lanes per site, one direction each, was measured slower: the warp then
+// touches 4 widely separated link planes per load and issues 4x the index math.)
 //
 // EPI_PLAIN:     out = D in
 // EPI_MDAGM:     out = m4 center - D in
 // EPI_MDAGM_DOT: as EPI_MDAGM, plus sum_s Re<center, out> per system -> FIN_ALPHA
 // EPI_RESID:     (FP64) out = b - (m4 x - D in), stored at the output precision,
 //                plus ||b - A x||^2 per system (FP64) -> FIN_RESID
-constexpr int LANES_PER_SITE = 4;
-
-template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT>
+template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
+  constexpr int DPL = 4 / LANES;  // directions per lane
   const Geom g = a.g;
   const int Ve = g.Ve;
   const int G = a.ngroups;
   const int grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
   const int j0 = grp * NS;
-  const int mu = threadIdx.x & 3;
-  const int s = bx * (BT / LANES_PER_SITE) + (threadIdx.x >> 2);
+  const int lane = LANES == 1 ? 0 : (int)(threadIdx.x % LANES);
+  const int s = bx * (BT / LANES) + (int)(threadIdx.x / LANES);
   const bool valid = s < Ve;
   bool act[NS];
   R m4[NS];
@@ -541,48 +594,51 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   if (any && valid) {
     int x[4];
     site_coords(g, P, s, x);
-    const int Lmu = mu == 0 ? g.L0 : mu == 1 ? g.L1 : mu == 2 ? g.L2 : g.L3;
-    int eb = 0;  // x_0 + ... + x_{mu-1}
-    if (mu > 0) eb += x[0];
-    if (mu > 1) eb += x[1];
-    if (mu > 2) eb += x[2];
-    const R eta = (eb & 1) ? R(-1) : R(1);
-    const int xm = x[mu];
-    int xf[4] = {x[0], x[1], x[2], x[3]};
-    int xb[4] = {x[0], x[1], x[2], x[3]};
-    xf[mu] = (xm + 1 == Lmu) ? 0 : xm + 1;
-    xb[mu] = (xm == 0) ? Lmu - 1 : xm - 1;
-    const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
-    const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
-    R bf = eta, bb = eta;
-    if (mu == 3 && g.ap) {
-      if (xm == g.L3 - 1) bf = -bf;
-      if (xm == 0) bb = -bb;
-    }
-    R uf[18], ub[18];
-    load_link<LP, RECON>(a.links, Ve, P, mu, s, uf);
-    load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, ub);
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      if (!act[k]) continue;
-      R vf[6], vb[6];
-      load_vec<VP>(a.in, k + j0, sf, Ve, vf);
-      load_vec<VP>(a.in, k + j0, sb, Ve, vb);
-      mv_acc(uf, vf, bf, acc[k]);
-      mvdag_acc(ub, vb, -bb, acc[k]);
+    for (int dd = 0; dd < DPL; ++dd) {
+      const int mu = lane * DPL + dd;
+      const int Lmu = mu == 0 ? g.L0 : mu == 1 ? g.L1 : mu == 2 ? g.L2 : g.L3;
+      int eb = 0;  // x_0 + ... + x_{mu-1}
+      if (mu > 0) eb += x[0];
+      if (mu > 1) eb += x[1];
+      if (mu > 2) eb += x[2];
+      const R eta = (eb & 1) ? R(-1) : R(1);
+      const int xm = x[mu];
+      int xf[4] = {x[0], x[1], x[2], x[3]};
+      int xb[4] = {x[0], x[1], x[2], x[3]};
+      xf[mu] = (xm + 1 == Lmu) ? 0 : xm + 1;
+      xb[mu] = (xm == 0) ? Lmu - 1 : xm - 1;
+      const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
+      const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
+      R bf = eta, bb = eta;
+      if (mu == 3 && g.ap) {
+        if (xm == g.L3 - 1) bf = -bf;
+        if (xm == 0) bb = -bb;
+      }
+      R uf[18], ub[18];
+      load_link<LP, RECON>(a.links, Ve, P, mu, s, uf);
+      load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, ub);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (!act[k]) continue;
+        R vf[6], vb[6];
+        load_vec<VP>(a.in, k + j0, sf, Ve, vf);
+        load_vec<VP>(a.in, k + j0, sb, Ve, vb);
+        mv_acc(uf, vf, bf, acc[k]);
+        mvdag_acc(ub, vb, -bb, acc[k]);
+      }
     }
   }
-  // sum the four directions: every lane of the site ends with the total
+  if (LANES > 1) {
 #pragma unroll
-  for (int k = 0; k < NS; ++k)
+    for (int k = 0; k < NS; ++k)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], 1);
-      acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], 2);
-    }
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int o = 1; o < LANES; o <<= 1) acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], o);
+  }
 
   if (any && valid) {
-    const int c = mu;  // colour written by this lane (lane 3: the scale)
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (!act[k]) continue;
@@ -596,8 +652,11 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         load_vec<VP>(a.center, j, s, Ve, cv);
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
-        if (EPI == EPI_MDAGM_DOT && c < 3) {
-          const R d = cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
+        if (EPI == EPI_MDAGM_DOT) {
+          R d = 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
           part[k][0] += (double)d;
         }
       } else {  // EPI_RESID (R = double)
@@ -606,9 +665,12 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         load_vec<P64>(a.aux, j, s, Ve, bv);
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
-        if (c < 3) part[k][0] += (double)o[2 * c] * (double)o[2 * c] + (double)o[2 * c + 1] * (double)o[2 * c + 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c % LANES == lane)
+            part[k][0] += (double)o[2 * c] * (double)o[2 * c] + (double)o[2 * c + 1] * (double)o[2 * c + 1];
       }
-      store_colour<OP>(a.out, j, s, Ve, c, o);
+      store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
     }
   }
 
