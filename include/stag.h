@@ -144,12 +144,14 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
                   int iters[], double true_res[]);
 
 /*
- * Average device time of one launch of the solver's half-operator kernel
- * D_oe at `precision` (the dominant kernel of the CG iteration), measured with
- * CUDA events around `nlaunch` back-to-back launches on the context stream,
- * on the context's own internal vectors with the CG's launch configuration.
- * `bytes_per_launch` (may be NULL) receives the kernel's algorithmic bytes
- * per launch: 8 links + 1 input vector + 1 output vector per output site.
+ * Average device time of one launch of the solver's first half-operator
+ * kernel at `precision` -- t = D_oe (r + beta p), the direction update fused
+ * into the neighbour gather, the dominant kernel of the CG iteration --
+ * measured with CUDA events around `nlaunch` back-to-back launches on the
+ * context stream, on the context's own internal vectors with the CG's launch
+ * configuration.  `bytes_per_launch` (may be NULL) receives the kernel's
+ * algorithmic bytes per launch: per output site 8 links, the two input
+ * vectors r and p once, and the output vector once.
  */
 int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_launch,
                      double *bytes_per_launch);

@@ -409,15 +409,16 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.partials2.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.cstride));
   const size_t ntickets = (size_t)nsys + 1 + (size_t)nsys * w.cstride;
   CK(w.tickets.ensure(sizeof(unsigned) * ntickets));
-  CK(w.flags.ensure(sizeof(int) * 2));
+  CK(w.flags.ensure(sizeof(int) * 4));
   CK(w.h_st.ensure(sizeof(SysState) * nsys));
-  CK(w.h_flags.ensure(sizeof(int) * 2));
+  CK(w.h_flags.ensure(sizeof(int) * 4));
   CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * ntickets, c->stream));
   CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
   // defined contents for the timing entry point before any solve
   CK(cudaMemsetAsync(w.p.data.p, 0, w.p.data.n, c->stream));
   if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
   CK(cudaMemsetAsync(w.x64.data.p, 0, w.x64.data.n, c->stream));
+  CK(cudaMemsetAsync(w.r.data.p, 0, w.r.data.n, c->stream));
   // pick the thread mapping of the inner and the FP64 half operators
   const void *lo = nullptr;
   CKS(links_for(c, prec, &lo));
@@ -480,20 +481,22 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.ngroups = w.G;
   a.ctl = ctl;
   a.gate = GATE_RUNNING;
-  // K1: t = D_oe p
+  a.aux = w.r.arg();
+  // K1: t = D_oe (r + beta p_old)
   a.par_out = 1;
   a.in = w.p.arg();
   a.out = w.t.arg();
   a.fin = FIN_NONE;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
-  // K2: Ap = 4 m^2 p - D_eo t, <p, Ap>
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s,
+                   a));
+  // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; <p, Ap>
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.out = w.Ap.arg();
   a.fin = FIN_ALPHA;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s,
-                   a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT_XPAY, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G,
+                   s, a));
   // K3: r -= alpha Ap, x += alpha p, ||r||^2
   BlasArgs b = blas_base(c, ctl);
   b.gate = GATE_RUNNING;
@@ -530,15 +533,10 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   return STAG_OK;
 }
 
-// K7
-int enqueue_xpay(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
-  Work &w = c->w;
-  BlasArgs b = blas_base(c, ctl);
-  b.gate = GATE_RUNNING;
-  b.fin = FIN_NONE;
-  CK(launch_xpay(w.VP, w.RP, w.NS, w.nbx_bl * w.G, s, b));
-  return STAG_OK;
-}
+// Iterations per pass of the solve loop: the body holds SOLVE_UNROLL copies of
+// K1..K3 and one conditional reliable update (a pending update waits for the
+// end of the pass), which spreads the loop and conditional-node overhead.
+constexpr int SOLVE_UNROLL = 4;
 
 int build_graph_inner(stag_ctx *c);
 
@@ -577,7 +575,8 @@ int build_graph_inner(stag_ctx *c) {
   const Ctl ctl = work_ctl(c, true);
 
   CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  int st = enqueue_main(c, c->cap, ctl);
+  int st = STAG_OK;
+  for (int u = 0; u < SOLVE_UNROLL && st == STAG_OK; ++u) st = enqueue_main(c, c->cap, ctl);
   if (st != STAG_OK) {
     cudaGraph_t tmp;
     cudaStreamEndCapture(c->cap, &tmp);
@@ -604,12 +603,10 @@ int build_graph_inner(stag_ctx *c) {
     CK(cudaStreamEndCapture(c->cap2, &tmp));
   }
   if (st != STAG_OK) return st;
-  st = enqueue_xpay(c, c->cap, ctl);
   {
     cudaGraph_t tmp;
     CK(cudaStreamEndCapture(c->cap, &tmp));
   }
-  if (st != STAG_OK) return st;
   CK(cudaGraphInstantiate(&w.exec, g, 0));
   return STAG_OK;
 }
@@ -641,6 +638,15 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
   }
   CK(cudaMemcpyAsync(w.st.p, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, c->stream));
   {
+    // loop-pass counter and its cap (an absolute bound on the solve loop)
+    int *hf = (int *)w.h_flags.p;
+    hf[0] = 1;
+    hf[1] = 0;
+    hf[2] = 0;
+    hf[3] = maxiter + 8;
+    CK(cudaMemcpyAsync(w.flags.p, hf, sizeof(int) * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  {
     const Ctl ctl0 = work_ctl(c, false);
     BlasArgs b = blas_base(c, ctl0);
     b.gate = GATE_NONE;
@@ -667,12 +673,12 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
   if (!ran) {
     const Ctl ctl = work_ctl(c, false);
     int *hf = (int *)w.h_flags.p;
-    const int chunk = 16;
-    for (long long it = 0; it <= (long long)maxiter + chunk; it += chunk) {
-      for (int i = 0; i < chunk; ++i) {
-        CKS(enqueue_main(c, c->stream, ctl));
+    const int passes_per_poll = 4;  // the same sequence as the graph body, polled every 4 passes
+    for (long long it = 0; it <= (long long)maxiter + 2 * SOLVE_UNROLL * passes_per_poll;
+         it += SOLVE_UNROLL * passes_per_poll) {
+      for (int i = 0; i < passes_per_poll; ++i) {
+        for (int u = 0; u < SOLVE_UNROLL; ++u) CKS(enqueue_main(c, c->stream, ctl));
         CKS(enqueue_update(c, c->stream, ctl));
-        CKS(enqueue_xpay(c, c->stream, ctl));
       }
       CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
@@ -951,15 +957,16 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   a.fin = FIN_NONE;
   a.par_out = 1;
   a.in = w.p.arg();
+  a.aux = w.r.arg();
   a.out = w.t.arg();
   const int nb = ds_blocks(c->Ve, w.lanes) * w.G;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -970,7 +977,9 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   if (bytes_per_launch) {
     const double lb = (double)cplx_bytes(w.prec) * (w.recon ? 6 : 9);
     const double vb = (double)cplx_bytes(w.VP) * 3 + ((w.VP == P16 || w.VP == PBF) ? 4 : 0);
-    *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * 2.0 * vb);
+    const double rb = (double)cplx_bytes(w.RP) * 3;
+    // links once; p_old and r once (through cache); t written once
+    *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * (2.0 * vb + rb));
   }
   return STAG_OK;
 }

@@ -25,11 +25,6 @@ cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, in
     k_axpy_norm<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);       \
     return cudaGetLastError();                                                 \
   }
-#define STAG_XPAY(VP_, RP_, NS_)                                               \
-  if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
-    k_xpay<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);            \
-    return cudaGetLastError();                                                 \
-  }
 #define STAG_INIT(VP_, RP_, NS_)                                               \
   if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
     k_cg_init<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);         \
@@ -40,13 +35,6 @@ cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t s
   STAG_BLAS_PAIRS(STAG_AXPY, 1)
   STAG_BLAS_PAIRS(STAG_AXPY, 4)
   STAG_BLAS_PAIRS(STAG_AXPY, 8)
-  return cudaErrorNotSupported;
-}
-
-cudaError_t launch_xpay(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
-  STAG_BLAS_PAIRS(STAG_XPAY, 1)
-  STAG_BLAS_PAIRS(STAG_XPAY, 4)
-  STAG_BLAS_PAIRS(STAG_XPAY, 8)
   return cudaErrorNotSupported;
 }
 

@@ -12,8 +12,10 @@
     return cudaGetLastError();                                                           \
   }
 
-// plain, mass epilogue, mass epilogue + dot
+// operator calls (plain, mass epilogue) and the two CG kernels (xpay fused
+// into the neighbour gather; xpay + mass epilogue + <p, Ap>)
 #define STAG_DS_EPIS(LP_, RC_, VP_, OP_, NS_)                \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN)          \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM)          \
-  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM_DOT)
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN_XPAY)     \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM_DOT_XPAY)

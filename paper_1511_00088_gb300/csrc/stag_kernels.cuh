@@ -85,10 +85,12 @@ struct SysState {
   double true_res;  // ||b - A x|| / ||b|| at the last reliable update
   double tol;       // stop when ||b - A x|| / ||b|| <= tol
   double delta;     // reliable update when ||r|| < delta * rmax (0: only at tol)
+  double rho_prev;  // ||r||^2 one iteration back (beta after a reliable update)
   int maxiter;
   int iter;
-  int done;         // 0 running, 1 converged, 2 iteration cap, -5 breakdown
-  int update;       // a reliable update is due this iteration
+  int done;         // 0 running, 3 stopped until the pending FP64 check, 1 converged,
+                    // 2 iteration cap, -5 breakdown
+  int update;       // a reliable update is pending (run at the end of the unrolled block)
   int n_updates;
   int pad_;
 };
@@ -100,7 +102,8 @@ struct Ctl {
   unsigned *grp_ticket;  // [ngroups]
   unsigned *chunk_ticket;  // [ngroups][cstride]
   unsigned *all_ticket;  // [1]
-  int *flags;            // [0] any system running, [1] any reliable update due
+  int *flags;            // [0] any system running, [1] any reliable update due,
+                         // [2] passes of the norm kernel this solve, [3] cap on [2]
   int pstride;           // partial slots per (system, value)
   int cstride;           // chunk slots per (system, value) = ceil(pstride / RED_CHUNK)
   int use_graph_cond;    // call cudaGraphSetConditional on the handles below
@@ -108,17 +111,18 @@ struct Ctl {
 };
 
 enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_UPDATE = 2 };
-enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_MDAGM_DOT = 2, EPI_RESID = 3 };
+enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_PLAIN_XPAY = 2, EPI_RESID = 3, EPI_MDAGM_DOT_XPAY = 4 };
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_NORM = 2, FIN_RESID = 3, FIN_INIT = 4 };
 
 struct DsArgs {
   Geom g;
   int par_out;           // parity of the output sites
   const void *links;     // [2][4][NE][Ve] of the link storage type
-  VecArg in;             // input on the other parity
-  VecArg center;         // EPI_MDAGM*: the vector the mass term multiplies; EPI_RESID: x
+  VecArg in;             // input on the other parity (the *_XPAY forms: p_old)
+  VecArg center;         // EPI_MDAGM: the vector the mass term multiplies; EPI_RESID: x;
+                         // EPI_MDAGM_DOT_XPAY: p (read p_old, written p_new)
   VecArg out;            // output (EPI_RESID: the reduced-precision residual)
-  VecArg aux;            // EPI_RESID: the source b (FP64)
+  VecArg aux;            // EPI_RESID: the source b (FP64); *_XPAY: the residual r
   double m4_single;      // 4 m^2 when ctl == nullptr
   int nsys, ngroups;
   Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
@@ -363,9 +367,19 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
   if (gate == GATE_NONE || c.st == nullptr) return true;
   const SysState &s = c.st[j];
   if (gate == GATE_RUNNING) return s.done == 0;
-  return s.done == 0 && s.update != 0;
+  return (s.done == 0 || s.done == 3) && s.update != 0;
 }
 
+// Per-system scalar logic of the CG iteration, run once per reduction by the
+// thread that holds the FP64 sums.
+//   FIN_ALPHA: alpha = rho / <p, Ap>  (breakdown if <p, Ap> <= 0 or not finite)
+//   FIN_NORM:  rho_new = ||r||^2; beta = rho_new / rho; a reliable update becomes
+//              pending when ||r|| < delta r_max; when ||r|| <= tol ||b|| or the
+//              iteration cap is reached the system stops (done = 3) until the
+//              pending FP64 recomputation decides
+//   FIN_RESID: true residual from the FP64 recomputation: converged, capped, or
+//              continue with rho = ||r_true||^2 and beta = rho / rho_prev
+//   FIN_INIT:  ||b||^2 and ||r||^2 of the starting residual
 __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, const double *sum) {
   SysState &s = c.st[j];
   if (fin == FIN_ALPHA) {
@@ -383,18 +397,15 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
       s.done = -5;
       return;
     }
-    if (s.iter > s.maxiter + 2) {
-      // hard stop: the forced update at maxiter did not run
-      s.done = 2;
-      return;
-    }
+    s.rho_prev = s.rho;
+    s.beta = rr / s.rho;
+    s.rho = rr;
     const double rn = sqrt(rr);
-    const double bn = sqrt(s.bnorm2);
-    if (rn < s.delta * s.rmax || rn <= s.tol * bn || s.iter >= s.maxiter) {
-      s.update = 1;  // beta and rho are set after the FP64 recomputation
-    } else {
-      s.beta = rr / s.rho;
-      s.rho = rr;
+    if (rn <= s.tol * sqrt(s.bnorm2) || s.iter >= s.maxiter) {
+      s.update = 1;
+      s.done = 3;
+    } else if (rn < s.delta * s.rmax) {
+      s.update = 1;
     }
   } else if (fin == FIN_RESID) {
     const double rr = sum[0];
@@ -411,12 +422,14 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
     } else if (s.iter >= s.maxiter) {
       s.done = 2;
     } else {
-      s.beta = rr / s.rho;
+      s.done = 0;
+      s.beta = rr / s.rho_prev;
       s.rho = rr;
     }
   } else if (fin == FIN_INIT) {
     s.bnorm2 = sum[0];
     s.rho = sum[1];
+    s.rho_prev = sum[1];
     s.rmax = sqrt(sum[0]);
     s.iter = 0;
     s.update = 0;
@@ -442,8 +455,17 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
 // few loads per lane.
 constexpr int RED_CHUNK = 64;
 
-template <int NS, int NV>
-__device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, double (&val)[NS][NV], int grp,
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// T = float: the per-thread values and the 32-lane tree are FP32 (GB300 runs
+// FP64 at a small fraction of the FP32 rate); every sum across warps and
+// blocks is FP64.  T = double: FP64 throughout (FP64 kernels).
+template <int NS, int NV, class T>
+__device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, T (&val)[NS][NV], int grp,
                                                     int ngroups, int j0, int nsys, int bx, int nbx) {
   __shared__ double red[32][NS * NV];
   __shared__ int am_last;
@@ -452,8 +474,8 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
   for (int k = 0; k < NS; ++k)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double w = warp_sum(val[k][v]);
-      if (lane == 0) red[warp][k * NV + v] = w;
+      const T w = warp_sum(val[k][v]);
+      if (lane == 0) red[warp][k * NV + v] = (double)w;
     }
   __syncthreads();
   const int chunk = bx / RED_CHUNK;
@@ -516,7 +538,7 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
       {
         const int done = __ldcg(&c.st[j].done), upd = __ldcg(&c.st[j].update);
         if (fin == FIN_INIT) part = true;
-        else if (fin == FIN_RESID) part = (done == 0 && upd != 0);
+        else if (fin == FIN_RESID) part = ((done == 0 || done == 3) && upd != 0);
         else part = (done == 0);
       }
       if (part) finalize_system(c, fin, j, sums[k]);
@@ -528,10 +550,17 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
       __threadfence();
       int running = 0, upd = 0;
       for (int j = 0; j < nsys; ++j) {
-        if (__ldcg(&c.st[j].done) == 0) {
+        const int done = __ldcg(&c.st[j].done);
+        if (done == 0 || done == 3) {
           running = 1;
           if (__ldcg(&c.st[j].update)) upd = 1;
         }
+      }
+      if (fin == FIN_NORM) {
+        // absolute bound on the number of loop passes, whatever the state says
+        const int passes = c.flags[2] + 1;
+        c.flags[2] = passes;
+        if (passes > c.flags[3]) running = 0;
       }
       c.flags[0] = running;
       c.flags[1] = upd;
@@ -562,6 +591,8 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, doubl
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
+  constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
+  constexpr bool XPAY = (EPI == EPI_PLAIN_XPAY || EPI == EPI_MDAGM_DOT_XPAY);
   constexpr int DPL = 4 / LANES;  // directions per lane
   const Geom g = a.g;
   const int Ve = g.Ve;
@@ -572,17 +603,19 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   const int s = bx * (BT / LANES) + (int)(threadIdx.x / LANES);
   const bool valid = s < Ve;
   bool act[NS];
-  R m4[NS];
+  R m4[NS], beta[NS];
   bool any = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     act[k] = sys_gate(a.ctl, a.gate, j0 + k, a.nsys);
     any |= act[k];
-    m4[k] = (R)((a.ctl.st != nullptr && j0 + k < a.nsys) ? a.ctl.st[j0 + k].m4 : a.m4_single);
+    const bool has = a.ctl.st != nullptr && j0 + k < a.nsys;
+    m4[k] = (R)(has ? a.ctl.st[j0 + k].m4 : a.m4_single);
+    beta[k] = (R)(has ? a.ctl.st[j0 + k].beta : 0.0);
   }
-  double part[NS][1];
+  R part[NS][1];  // per-thread reduction values (FP32 in the FP32-arithmetic kernels)
 #pragma unroll
-  for (int k = 0; k < NS; ++k) part[k][0] = 0.0;
+  for (int k = 0; k < NS; ++k) part[k][0] = 0;
 
   R acc[NS][6];
 #pragma unroll
@@ -624,6 +657,16 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         R vf[6], vb[6];
         load_vec<VP>(a.in, k + j0, sf, Ve, vf);
         load_vec<VP>(a.in, k + j0, sb, Ve, vb);
+        if (XPAY) {  // the operator acts on p_new = r + beta p_old, formed here
+          R rf[6], rb[6];
+          load_vec<RP>(a.aux, k + j0, sf, Ve, rf);
+          load_vec<RP>(a.aux, k + j0, sb, Ve, rb);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            vf[i] = rf[i] + beta[k] * vf[i];
+            vb[i] = rb[i] + beta[k] * vb[i];
+          }
+        }
         mv_acc(uf, vf, bf, acc[k]);
         mvdag_acc(ub, vb, -bb, acc[k]);
       }
@@ -644,21 +687,32 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
       if (!act[k]) continue;
       const int j = k + j0;
       R o[6];
-      if (EPI == EPI_PLAIN) {
+      if (EPI == EPI_PLAIN || EPI == EPI_PLAIN_XPAY) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = acc[k][i];
-      } else if (EPI == EPI_MDAGM || EPI == EPI_MDAGM_DOT) {
+      } else if (EPI == EPI_MDAGM) {
         R cv[6];
         load_vec<VP>(a.center, j, s, Ve, cv);
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
-        if (EPI == EPI_MDAGM_DOT) {
-          R d = 0;
+      } else if (EPI == EPI_MDAGM_DOT_XPAY) {
+        // p_new = r + beta p_old at this site (as the previous kernel formed it at
+        // the neighbours), Ap = m4 p_new - D_eo t, <p_new, Ap>; p_new is stored
+        R cv[6], rv[6];
+        load_vec_rw<VP>(a.center, j, s, Ve, cv);
+        load_vec<RP>(a.aux, j, s, Ve, rv);
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
-          part[k][0] += (double)d;
+        for (int i = 0; i < 6; ++i) {
+          cv[i] = rv[i] + beta[k] * cv[i];
+          o[i] = m4[k] * cv[i] - acc[k][i];
         }
+        R d = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
+        part[k][0] += d;
+        if (LANES > 1) __syncwarp();  // every lane has read p_old before any lane writes p_new
+        store_site_share<VP, LANES>(a.center, j, s, Ve, lane, cv);
       } else {  // EPI_RESID (R = double)
         R xx[6], bv[6];
         load_vec<P64>(a.center, j, s, Ve, xx);
@@ -667,14 +721,13 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         for (int i = 0; i < 6; ++i) o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (c % LANES == lane)
-            part[k][0] += (double)o[2 * c] * (double)o[2 * c] + (double)o[2 * c + 1] * (double)o[2 * c + 1];
+          if (c % LANES == lane) part[k][0] += o[2 * c] * o[2 * c] + o[2 * c + 1] * o[2 * c + 1];
       }
       store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
     }
   }
 
-  if (EPI == EPI_MDAGM_DOT || EPI == EPI_RESID) {
+  if (EPI == EPI_MDAGM_DOT_XPAY || EPI == EPI_RESID) {
     if (a.ctl.st != nullptr) reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
   }
 }
@@ -689,9 +742,9 @@ __global__ void __launch_bounds__(BT) k_axpy_norm(const BlasArgs a) {
   const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
   const int j0 = grp * NS, Ve = a.Ve;
   const int s = bx * BT + threadIdx.x;
-  double part[NS][1];
+  R part[NS][1];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) part[k][0] = 0.0;
+  for (int k = 0; k < NS; ++k) part[k][0] = 0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const int j = j0 + k;
@@ -711,31 +764,9 @@ __global__ void __launch_bounds__(BT) k_axpy_norm(const BlasArgs a) {
     }
     store_vec<RP>(a.r, j, s, Ve, r);
     store_vec<RP>(a.x, j, s, Ve, x);
-    part[k][0] = (double)nn;
+    part[k][0] = nn;
   }
   reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
-}
-
-// p = r + beta p
-template <int VP, int RP, int NS, int BT>
-__global__ void __launch_bounds__(BT) k_xpay(const BlasArgs a) {
-  typedef typename Tr<RP>::R R;
-  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G;
-  const int j0 = grp * NS, Ve = a.Ve;
-  const int s = bx * BT + threadIdx.x;
-  if (s >= Ve) return;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const int j = j0 + k;
-    if (!sys_gate(a.ctl, a.gate, j, a.nsys)) continue;
-    const R beta = (R)a.ctl.st[j].beta;
-    R p[6], r[6];
-    load_vec_rw<VP>(a.p, j, s, Ve, p);
-    load_vec<RP>(a.r, j, s, Ve, r);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) p[i] = r[i] + beta * p[i];
-    store_vec<VP>(a.p, j, s, Ve, p);
-  }
 }
 
 // reliable update, part 1: x64 += x_lo; x_lo = 0 (systems with an update due)
@@ -762,8 +793,8 @@ __global__ void __launch_bounds__(BT) k_accum_x(const BlasArgs a) {
   }
 }
 
-// CG start: x64 = 0, x_lo = 0, r = round(b), p = round(r);
-// partials ||b||^2 (FP64) and ||r||^2 -> FIN_INIT
+// CG start: x64 = 0, x_lo = 0, r = round(b), p_old = 0 (with beta = 0 the
+// first half operator forms p = r); partials ||b||^2 (FP64), ||r||^2 -> FIN_INIT
 template <int VP, int RP, int NS, int BT>
 __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
   typedef typename Tr<RP>::R R;
@@ -794,7 +825,8 @@ __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
     R rr = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) rr += rr_[i] * rr_[i];
-    store_vec<VP>(a.p, j, s, Ve, rr_);
+    // p_old = 0 and beta = 0: the first iteration forms p = r itself
+    store_vec<VP>(a.p, j, s, Ve, z);
     store_vec<RP>(a.x, j, s, Ve, z);
     store_vec<P64>(a.x64, j, s, Ve, z64);
     part[k][0] = bb;
