@@ -592,7 +592,7 @@ template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
-  constexpr bool XPAY = (EPI == EPI_PLAIN_XPAY || EPI == EPI_MDAGM_DOT_XPAY);
+  constexpr bool XPAY_GATHER = (EPI == EPI_PLAIN_XPAY);  // fold r + beta p into the neighbour gather
   constexpr int DPL = 4 / LANES;  // directions per lane
   const Geom g = a.g;
   const int Ve = g.Ve;
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         R vf[6], vb[6];
         load_vec<VP>(a.in, k + j0, sf, Ve, vf);
         load_vec<VP>(a.in, k + j0, sb, Ve, vb);
-        if (XPAY) {  // the operator acts on p_new = r + beta p_old, formed here
+        if (XPAY_GATHER) {  // the operator acts on p_new = r + beta p_old, formed here
           R rf[6], rb[6];
           load_vec<RP>(a.aux, k + j0, sf, Ve, rf);
           load_vec<RP>(a.aux, k + j0, sb, Ve, rb);
@@ -681,11 +681,40 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         for (int o = 1; o < LANES; o <<= 1) acc[k][i] += __shfl_xor_sync(0xffffffffu, acc[k][i], o);
   }
 
-  if (any && valid) {
+  // The epilogue loop runs on every lane (act[] is uniform across the block) so
+  // that the warp barrier of the fused direction update is reached by all
+  // lanes; per-lane work is predicated on `valid`.
+  if (any) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (!act[k]) continue;
       const int j = k + j0;
+      if (EPI == EPI_MDAGM_DOT_XPAY) {
+        // p_new = r + beta p_old at this site (as the previous kernel formed it at
+        // the neighbours), Ap = m4 p_new - D_eo t, <p_new, Ap>; p_new is stored
+        R cv[6], rv[6], o[6];
+        if (valid) {
+          load_vec_rw<VP>(a.center, j, s, Ve, cv);
+          load_vec<RP>(a.aux, j, s, Ve, rv);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            cv[i] = rv[i] + beta[k] * cv[i];
+            o[i] = m4[k] * cv[i] - acc[k][i];
+          }
+          R d = 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
+          part[k][0] += d;
+        }
+        if (LANES > 1) __syncwarp();  // every lane has read p_old before any lane writes p_new
+        if (valid) {
+          store_site_share<VP, LANES>(a.center, j, s, Ve, lane, cv);
+          store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
+        }
+        continue;
+      }
+      if (!valid) continue;
       R o[6];
       if (EPI == EPI_PLAIN || EPI == EPI_PLAIN_XPAY) {
 #pragma unroll
@@ -695,24 +724,6 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         load_vec<VP>(a.center, j, s, Ve, cv);
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
-      } else if (EPI == EPI_MDAGM_DOT_XPAY) {
-        // p_new = r + beta p_old at this site (as the previous kernel formed it at
-        // the neighbours), Ap = m4 p_new - D_eo t, <p_new, Ap>; p_new is stored
-        R cv[6], rv[6];
-        load_vec_rw<VP>(a.center, j, s, Ve, cv);
-        load_vec<RP>(a.aux, j, s, Ve, rv);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          cv[i] = rv[i] + beta[k] * cv[i];
-          o[i] = m4[k] * cv[i] - acc[k][i];
-        }
-        R d = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
-        part[k][0] += d;
-        if (LANES > 1) __syncwarp();  // every lane has read p_old before any lane writes p_new
-        store_site_share<VP, LANES>(a.center, j, s, Ve, lane, cv);
       } else {  // EPI_RESID (R = double)
         R xx[6], bv[6];
         load_vec<P64>(a.center, j, s, Ve, xx);
