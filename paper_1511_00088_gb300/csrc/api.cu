@@ -4,22 +4,24 @@
 // precision part).
 //
 // CG driver.  Per iteration, for every running system j (all on the GPU, no
-// host round trip):
-//   K1  t   = D_oe p                                  (inner precision)
-//   K2  Ap  = 4 m_j^2 p - D_eo t,  <p, Ap>  -> alpha  (FP64 reduction)
-//   K3  r  -= alpha Ap,  x_lo += alpha p,  ||r||^2    (FP64 reduction)
-//       ||r|| < delta * r_max or ||r|| <= tol ||b|| -> reliable update due
-//   if an update is due (a conditional graph node):
+// host round trip), two kernels:
+//   K1  p = r + beta p_old formed in the neighbour gather; t = D_oe p;
+//       |t|^2 and |p|^2 -> alpha = rho / (4 m_j^2 |p|^2 + |t|^2)
+//       (= <p, A p>, as D_eo^dag = -D_oe)                  (FP64 reduction)
+//   K2  p = r + beta p_old at the centre (stored); A p = 4 m^2 p - D_eo t;
+//       r -= alpha A p; x_lo += alpha p; |r|^2 -> beta; reliable-update and
+//       convergence triggers                              (FP64 reduction)
+//   if a reliable update is pending (a conditional graph node at the end of
+//   every SOLVE_UNROLL iterations):
 //   K4  x64 += x_lo,  x_lo = 0
-//   K5  t64 = D_oe x64                                (FP64)
+//   K5  t64 = D_oe x64                                    (FP64)
 //   K6  r = b - (4 m^2 x64 - D_eo t64) in FP64, stored at the residual's
 //       precision; ||r||^2 in FP64 -> true residual, convergence, beta
-//   K7  p = r + beta p
-// The iteration sits in the body of a CUDA-graph WHILE node whose condition
-// the last block of K3 / K6 sets ("any system still running"); the update
-// kernels sit in an IF node set by K3.  One graph launch runs the whole solve.
-// Without conditional-node support the same kernels run eagerly, with the
-// host polling a device flag every few iterations.
+// The iterations sit in the body of a CUDA-graph WHILE node whose condition
+// the last block of K2 / K6 sets ("any system still running"); the update
+// kernels sit in an IF node set by K2.  One graph launch runs the whole solve.
+// Without conditional-node support the same kernel sequence runs eagerly, with
+// the host polling a device flag every few loop passes.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -112,12 +114,12 @@ struct PinnedBuf {
 // solver workspace for one (number of systems, precision, link format)
 struct Work {
   int nsys = 0, prec = -1, recon = -1;
-  int VP = P32;  // precision of the Krylov vectors p, Ap, t
+  int VP = P32;  // precision of the Krylov vectors p and t
   int RP = P32;  // precision of the iterated residual r and partial solution x_lo
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
   int nbx_bl = 0, pstride = 0, cstride = 0;
-  VecBuf b64, x64, t64, r, x, p, Ap, t;
+  VecBuf b64, x64, t64, r, x, p, t;
   DevBuf st, partials, partials2, tickets, flags;
   PinnedBuf h_st, h_flags;
   cudaGraph_t graph = nullptr;
@@ -402,7 +404,6 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.r.ensure(w.RP, nsys, Ve));
   CK(w.x.ensure(w.RP, nsys, Ve));
   CK(w.p.ensure(VP, nsys, Ve));
-  CK(w.Ap.ensure(VP, nsys, Ve));
   CK(w.t.ensure(VP, nsys, Ve));
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
@@ -459,7 +460,6 @@ BlasArgs blas_base(stag_ctx *c, const Ctl &ctl) {
   memset(&b, 0, sizeof b);
   b.Ve = c->Ve;
   b.p = w.p.arg();
-  b.Ap = w.Ap.arg();
   b.r = w.r.arg();
   b.x = w.x.arg();
   b.b = w.b64.arg();
@@ -482,26 +482,19 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.ctl = ctl;
   a.gate = GATE_RUNNING;
   a.aux = w.r.arg();
-  // K1: t = D_oe (r + beta p_old)
+  a.xlo = w.x.arg();
+  // K1: t = D_oe (r + beta p_old); |t|^2, |p|^2 -> alpha
   a.par_out = 1;
   a.in = w.p.arg();
   a.out = w.t.arg();
-  a.fin = FIN_NONE;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s,
-                   a));
-  // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; <p, Ap>
+  a.fin = FIN_ALPHA;
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
+  // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
-  a.out = w.Ap.arg();
-  a.fin = FIN_ALPHA;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_MDAGM_DOT_XPAY, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G,
-                   s, a));
-  // K3: r -= alpha Ap, x += alpha p, ||r||^2
-  BlasArgs b = blas_base(c, ctl);
-  b.gate = GATE_RUNNING;
-  b.fin = FIN_NORM;
-  CK(launch_axpy_norm(w.VP, w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  a.fin = FIN_NORM;
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
   return STAG_OK;
 }
 
@@ -697,7 +690,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     if (hs[j].done == -5) status = STAG_ERR_BREAKDOWN;
     else if (hs[j].done != 1 && status == STAG_OK) status = STAG_NOT_CONVERGED;
   }
-  if (status == STAG_ERR_BREAKDOWN) c->err = "CG breakdown: <p,Ap> <= 0 or non-finite residual";
+  if (status == STAG_ERR_BREAKDOWN) c->err = "CG breakdown: <p, A p> not positive or a non-finite residual";
   else if (status == STAG_NOT_CONVERGED) c->err = "iteration cap reached before the tolerance";
   return status;
 }
@@ -963,10 +956,10 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN_XPAY, w.lanes, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;

@@ -20,23 +20,11 @@ cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, in
 #define STAG_BLAS_PAIRS(X, NS_) \
   X(P64, P64, NS_) X(P32, P32, NS_) X(P16, P32, NS_) X(PBF, P32, NS_)
 
-#define STAG_AXPY(VP_, RP_, NS_)                                               \
-  if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
-    k_axpy_norm<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);       \
-    return cudaGetLastError();                                                 \
-  }
 #define STAG_INIT(VP_, RP_, NS_)                                               \
   if (VP == VP_ && RP == RP_ && NS == NS_) {                                   \
     k_cg_init<VP_, RP_, NS_, BLAS_BT><<<nblocks, BLAS_BT, 0, st>>>(a);         \
     return cudaGetLastError();                                                 \
   }
-
-cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
-  STAG_BLAS_PAIRS(STAG_AXPY, 1)
-  STAG_BLAS_PAIRS(STAG_AXPY, 4)
-  STAG_BLAS_PAIRS(STAG_AXPY, 8)
-  return cudaErrorNotSupported;
-}
 
 cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a) {
   STAG_BLAS_PAIRS(STAG_INIT, 1)

@@ -12,10 +12,9 @@
     return cudaGetLastError();                                                           \
   }
 
-// operator calls (plain, mass epilogue) and the two CG kernels (xpay fused
-// into the neighbour gather; xpay + mass epilogue + <p, Ap>)
+// operator calls (plain, mass epilogue) and the two kernels of a CG iteration
 #define STAG_DS_EPIS(LP_, RC_, VP_, OP_, NS_)                \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN)          \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM)          \
-  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN_XPAY)     \
-  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM_DOT_XPAY)
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_CG_K1)          \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_CG_K2)

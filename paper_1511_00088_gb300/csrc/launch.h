@@ -29,7 +29,6 @@ cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int la
 cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a);
 
-cudaError_t launch_axpy_norm(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 

@@ -111,18 +111,19 @@ struct Ctl {
 };
 
 enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_UPDATE = 2 };
-enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_PLAIN_XPAY = 2, EPI_RESID = 3, EPI_MDAGM_DOT_XPAY = 4 };
+enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_CG_K1 = 2, EPI_RESID = 3, EPI_CG_K2 = 4 };
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_NORM = 2, FIN_RESID = 3, FIN_INIT = 4 };
 
 struct DsArgs {
   Geom g;
   int par_out;           // parity of the output sites
   const void *links;     // [2][4][NE][Ve] of the link storage type
-  VecArg in;             // input on the other parity (the *_XPAY forms: p_old)
+  VecArg in;             // input on the other parity (EPI_CG_K1: p_old)
   VecArg center;         // EPI_MDAGM: the vector the mass term multiplies; EPI_RESID: x;
-                         // EPI_MDAGM_DOT_XPAY: p (read p_old, written p_new)
+                         // EPI_CG_K2: p (read p_old, written p_new)
   VecArg out;            // output (EPI_RESID: the reduced-precision residual)
-  VecArg aux;            // EPI_RESID: the source b (FP64); *_XPAY: the residual r
+  VecArg aux;            // EPI_RESID: the source b (FP64); EPI_CG_K1/K2: the residual r
+  VecArg xlo;            // EPI_CG_K2: the partial solution x_lo (read and written)
   double m4_single;      // 4 m^2 when ctl == nullptr
   int nsys, ngroups;
   Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
@@ -131,7 +132,7 @@ struct DsArgs {
 
 struct BlasArgs {
   int Ve;
-  VecArg p, Ap, r, x, b, x64;   // meanings per kernel
+  VecArg p, r, x, b, x64;   // meanings per kernel
   int nsys, ngroups;
   Ctl ctl;
   int gate, fin;
@@ -372,7 +373,8 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
 
 // Per-system scalar logic of the CG iteration, run once per reduction by the
 // thread that holds the FP64 sums.
-//   FIN_ALPHA: alpha = rho / <p, Ap>  (breakdown if <p, Ap> <= 0 or not finite)
+//   FIN_ALPHA: alpha = rho / <p, Ap> with <p, Ap> = 4 m^2 |p|^2 + |D_oe p|^2
+//              (breakdown if it is not positive and finite)
 //   FIN_NORM:  rho_new = ||r||^2; beta = rho_new / rho; a reliable update becomes
 //              pending when ||r|| < delta r_max; when ||r|| <= tol ||b|| or the
 //              iteration cap is reached the system stops (done = 3) until the
@@ -383,7 +385,8 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
 __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, const double *sum) {
   SysState &s = c.st[j];
   if (fin == FIN_ALPHA) {
-    const double pAp = sum[0];
+    // <p, (4m^2 - D_eo D_oe) p> = 4 m^2 |p|^2 + |D_oe p|^2  (D_eo^dag = -D_oe)
+    const double pAp = s.m4 * sum[1] + sum[0];
     s.pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       s.done = -5;
@@ -583,16 +586,20 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, T (&v
 // (Four lanes per site, one direction each, was measured slower: the warp then
 // touches 4 widely separated link planes per load and issues 4x the index math.)
 //
-// EPI_PLAIN:     out = D in
-// EPI_MDAGM:     out = m4 center - D in
-// EPI_MDAGM_DOT: as EPI_MDAGM, plus sum_s Re<center, out> per system -> FIN_ALPHA
-// EPI_RESID:     (FP64) out = b - (m4 x - D in), stored at the output precision,
-//                plus ||b - A x||^2 per system (FP64) -> FIN_RESID
+// EPI_PLAIN:  out = D in
+// EPI_MDAGM:  out = m4 center - D in
+// EPI_CG_K1:  t = D_oe p_new with p_new = r + beta p_old formed in the gather;
+//             |t|^2 and |p_new|^2 per system -> FIN_ALPHA
+// EPI_CG_K2:  p_new (again, at the centre), Ap = m4 p_new - D_eo t,
+//             r -= alpha Ap, x_lo += alpha p_new; |r|^2 per system -> FIN_NORM
+// EPI_RESID:  (FP64) out = b - (m4 x - D in), stored at the output precision,
+//             plus ||b - A x||^2 per system (FP64) -> FIN_RESID
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
-  constexpr bool XPAY_GATHER = (EPI == EPI_PLAIN_XPAY);  // fold r + beta p into the neighbour gather
+  constexpr bool XPAY_GATHER = (EPI == EPI_CG_K1);  // fold r + beta p into the neighbour gather
+  constexpr int NV = (EPI == EPI_CG_K1) ? 2 : 1;     // reduction values per system
   constexpr int DPL = 4 / LANES;  // directions per lane
   const Geom g = a.g;
   const int Ve = g.Ve;
@@ -613,9 +620,11 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
     m4[k] = (R)(has ? a.ctl.st[j0 + k].m4 : a.m4_single);
     beta[k] = (R)(has ? a.ctl.st[j0 + k].beta : 0.0);
   }
-  R part[NS][1];  // per-thread reduction values (FP32 in the FP32-arithmetic kernels)
+  R part[NS][NV];  // per-thread reduction values (FP32 in the FP32-arithmetic kernels)
 #pragma unroll
-  for (int k = 0; k < NS; ++k) part[k][0] = 0;
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[k][v] = 0;
 
   R acc[NS][6];
 #pragma unroll
@@ -666,6 +675,14 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
             vf[i] = rf[i] + beta[k] * vf[i];
             vb[i] = rb[i] + beta[k] * vb[i];
           }
+          // |p_new|^2 over the even sites: each even site is the forward-x
+          // neighbour of exactly one odd site, so count it there
+          if (mu == 0 && NV > 1) {
+            R q = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) q += vf[i] * vf[i];
+            part[k][NV - 1] += q;
+          }
         }
         mv_acc(uf, vf, bf, acc[k]);
         mvdag_acc(ub, vb, -bb, acc[k]);
@@ -689,36 +706,49 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
     for (int k = 0; k < NS; ++k) {
       if (!act[k]) continue;
       const int j = k + j0;
-      if (EPI == EPI_MDAGM_DOT_XPAY) {
-        // p_new = r + beta p_old at this site (as the previous kernel formed it at
-        // the neighbours), Ap = m4 p_new - D_eo t, <p_new, Ap>; p_new is stored
-        R cv[6], rv[6], o[6];
+      if (EPI == EPI_CG_K2) {
+        // p_new = r + beta p_old at this site (as the first kernel formed it at the
+        // neighbours); Ap = 4 m^2 p_new - D_eo t; r -= alpha Ap; x_lo += alpha p_new;
+        // p_new, r, x_lo stored; |r|^2 reduced.  Ap itself is never stored.
+        R cv[6], rv[6], xv[6];
+        const R alpha = (R)a.ctl.st[j].alpha;
         if (valid) {
           load_vec_rw<VP>(a.center, j, s, Ve, cv);
-          load_vec<RP>(a.aux, j, s, Ve, rv);
+          load_vec_rw<RP>(a.aux, j, s, Ve, rv);
+          load_vec_rw<RP>(a.xlo, j, s, Ve, xv);
 #pragma unroll
           for (int i = 0; i < 6; ++i) {
             cv[i] = rv[i] + beta[k] * cv[i];
-            o[i] = m4[k] * cv[i] - acc[k][i];
+            const R ap = m4[k] * cv[i] - acc[k][i];
+            rv[i] -= alpha * ap;
+            xv[i] += alpha * cv[i];
           }
-          R d = 0;
+          R q = 0;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            if (c % LANES == lane) d += cv[2 * c] * o[2 * c] + cv[2 * c + 1] * o[2 * c + 1];
-          part[k][0] += d;
+            if (c % LANES == lane) q += rv[2 * c] * rv[2 * c] + rv[2 * c + 1] * rv[2 * c + 1];
+          part[k][0] += q;
         }
-        if (LANES > 1) __syncwarp();  // every lane has read p_old before any lane writes p_new
+        if (LANES > 1) __syncwarp();  // every lane has read the site before any lane writes it
         if (valid) {
           store_site_share<VP, LANES>(a.center, j, s, Ve, lane, cv);
-          store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
+          store_site_share<RP, LANES>(a.aux, j, s, Ve, lane, rv);
+          store_site_share<RP, LANES>(a.xlo, j, s, Ve, lane, xv);
         }
         continue;
       }
       if (!valid) continue;
       R o[6];
-      if (EPI == EPI_PLAIN || EPI == EPI_PLAIN_XPAY) {
+      if (EPI == EPI_PLAIN || EPI == EPI_CG_K1) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = acc[k][i];
+        if (EPI == EPI_CG_K1) {  // |t|^2 over the odd sites
+          R q = 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c % LANES == lane) q += o[2 * c] * o[2 * c] + o[2 * c + 1] * o[2 * c + 1];
+          part[k][0] += q;
+        }
       } else if (EPI == EPI_MDAGM) {
         R cv[6];
         load_vec<VP>(a.center, j, s, Ve, cv);
@@ -738,48 +768,14 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
     }
   }
 
-  if (EPI == EPI_MDAGM_DOT_XPAY || EPI == EPI_RESID) {
-    if (a.ctl.st != nullptr) reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+  if (EPI == EPI_CG_K1 || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
+    if (a.ctl.st != nullptr) reduce_and_finalize<NS, NV>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
   }
 }
 
 // ---------------------------------------------------------------------------
 // fused BLAS-1 steps of the CG iteration (one thread per site, NS systems)
 // ---------------------------------------------------------------------------
-// r -= alpha Ap; x += alpha p; ||r||^2 -> FIN_NORM.  p/Ap at VP, r/x at RP.
-template <int VP, int RP, int NS, int BT>
-__global__ void __launch_bounds__(BT) k_axpy_norm(const BlasArgs a) {
-  typedef typename Tr<RP>::R R;
-  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
-  const int j0 = grp * NS, Ve = a.Ve;
-  const int s = bx * BT + threadIdx.x;
-  R part[NS][1];
-#pragma unroll
-  for (int k = 0; k < NS; ++k) part[k][0] = 0;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const int j = j0 + k;
-    if (!sys_gate(a.ctl, a.gate, j, a.nsys) || s >= Ve) continue;
-    const R alpha = (R)a.ctl.st[j].alpha;
-    R p[6], ap[6], r[6], x[6];
-    load_vec<VP>(a.p, j, s, Ve, p);
-    load_vec<VP>(a.Ap, j, s, Ve, ap);
-    load_vec_rw<RP>(a.r, j, s, Ve, r);
-    load_vec_rw<RP>(a.x, j, s, Ve, x);
-    R nn = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      r[i] -= alpha * ap[i];
-      x[i] += alpha * p[i];
-      nn += r[i] * r[i];
-    }
-    store_vec<RP>(a.r, j, s, Ve, r);
-    store_vec<RP>(a.x, j, s, Ve, x);
-    part[k][0] = nn;
-  }
-  reduce_and_finalize<NS, 1>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
-}
-
 // reliable update, part 1: x64 += x_lo; x_lo = 0 (systems with an update due)
 template <int RP, int NS, int BT>
 __global__ void __launch_bounds__(BT) k_accum_x(const BlasArgs a) {
