@@ -118,9 +118,9 @@ struct Work {
   int RP = P32;  // precision of the iterated residual r and partial solution x_lo
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
-  int nbx_bl = 0, pstride = 0, cstride = 0;
+  int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
-  DevBuf st, partials, partials2, tickets, flags;
+  DevBuf st, partials, tickets, flags;
   PinnedBuf h_st, h_flags;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -397,7 +397,6 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   const int nbx_ds_max = ds_blocks(Ve, 2);
   w.nbx_bl = (Ve + BLAS_BT - 1) / BLAS_BT;
   w.pstride = nbx_ds_max > w.nbx_bl ? nbx_ds_max : w.nbx_bl;
-  w.cstride = (w.pstride + RED_CHUNK - 1) / RED_CHUNK;
   CK(w.b64.ensure(P64, nsys, Ve));
   CK(w.x64.ensure(P64, nsys, Ve));
   CK(w.t64.ensure(P64, nsys, Ve));
@@ -407,8 +406,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.t.ensure(VP, nsys, Ve));
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
-  CK(w.partials2.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.cstride));
-  const size_t ntickets = (size_t)nsys + 1 + (size_t)nsys * w.cstride;
+  const size_t ntickets = 1;
   CK(w.tickets.ensure(sizeof(unsigned) * ntickets));
   CK(w.flags.ensure(sizeof(int) * 4));
   CK(w.h_st.ensure(sizeof(SysState) * nsys));
@@ -434,13 +432,9 @@ Ctl work_ctl(stag_ctx *c, bool graph) {
   memset(&k, 0, sizeof k);
   k.st = (SysState *)w.st.p;
   k.partials = (double *)w.partials.p;
-  k.partials2 = (double *)w.partials2.p;
-  k.grp_ticket = (unsigned *)w.tickets.p;
-  k.all_ticket = (unsigned *)w.tickets.p + w.nsys;
-  k.chunk_ticket = (unsigned *)w.tickets.p + w.nsys + 1;
+  k.all_ticket = (unsigned *)w.tickets.p;
   k.flags = (int *)w.flags.p;
   k.pstride = w.pstride;
-  k.cstride = w.cstride;
   k.use_graph_cond = graph ? 1 : 0;
   k.h_loop = w.h_loop;
   k.h_update = w.h_update;
@@ -488,13 +482,16 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.in = w.p.arg();
   a.out = w.t.arg();
   a.fin = FIN_ALPHA;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
+  const int nbx = ds_blocks(c->Ve, w.lanes);
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nbx * w.G, s, a));
+  CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s));
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.fin = FIN_NORM;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes, nbx * w.G, s, a));
+  CK(launch_finalize(ctl, FIN_NORM, nbx, 1, w.nsys, s));
   return STAG_OK;
 }
 
@@ -523,11 +520,12 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.out = w.r.arg();
   a.fin = FIN_RESID;
   CK(launch_dslash(P64, 0, P64, w.RP, w.NS64, EPI_RESID, w.lanes64, ds_blocks(c->Ve, w.lanes64) * w.G64, s, a));
+  CK(launch_finalize(ctl, FIN_RESID, ds_blocks(c->Ve, w.lanes64), 1, w.nsys, s));
   return STAG_OK;
 }
 
 // Iterations per pass of the solve loop: the body holds SOLVE_UNROLL copies of
-// K1..K3 and one conditional reliable update (a pending update waits for the
+// K1, K2 (each followed by its finalize kernel) and one conditional reliable update (a pending update waits for the
 // end of the pass), which spreads the loop and conditional-node overhead.
 constexpr int SOLVE_UNROLL = 4;
 
@@ -645,6 +643,7 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     b.gate = GATE_NONE;
     b.fin = FIN_INIT;
     CK(launch_cg_init(w.VP, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
+    CK(launch_finalize(ctl0, FIN_INIT, w.nbx_bl, 2, nsys, c->stream));
   }
 
   bool ran = false;

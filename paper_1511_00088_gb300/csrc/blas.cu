@@ -45,7 +45,74 @@ cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const B
   return cudaErrorNotSupported;
 }
 
+// grid = nsys blocks of FIN_BT threads; block j reduces system j's nv partial
+// arrays of nbx entries each
+__global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys) {
+  __shared__ double red[FIN_BT / 32][NVMAX];
+  __shared__ double sums[NVMAX];
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = 0; v < nv; ++v) {
+    const double *p = c.partials + ((long long)j * NVMAX + v) * c.pstride;
+    double s0 = 0.0, s1 = 0.0;
+    int i = threadIdx.x;
+    for (; i + FIN_BT < nbx; i += 2 * FIN_BT) {
+      s0 += p[i];
+      s1 += p[i + FIN_BT];
+    }
+    if (i < nbx) s0 += p[i];
+    const double w = warp_sum(s0 + s1);
+    if (lane == 0) red[warp][v] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+    for (int w = 0; w < FIN_BT / 32; ++w) s += red[w][threadIdx.x];
+    sums[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  {
+    const int done = c.st[j].done, upd = c.st[j].update;
+    bool part;
+    if (fin == FIN_INIT) part = true;
+    else if (fin == FIN_RESID) part = ((done == 0 || done == 3) && upd != 0);
+    else part = (done == 0);
+    if (part) finalize_system(c, fin, j, sums);
+  }
+  __threadfence();
+  const unsigned t = atomicAdd(c.all_ticket, 1u);
+  if (t != (unsigned)(nsys - 1)) return;
+  *c.all_ticket = 0u;
+  __threadfence();
+  int running = 0, upd = 0;
+  for (int q = 0; q < nsys; ++q) {
+    const int done = __ldcg(&c.st[q].done);
+    if (done == 0 || done == 3) {
+      running = 1;
+      if (__ldcg(&c.st[q].update)) upd = 1;
+    }
+  }
+  if (fin == FIN_NORM) {
+    // absolute bound on the number of loop passes, whatever the state says
+    const int passes = c.flags[2] + 1;
+    c.flags[2] = passes;
+    if (passes > c.flags[3]) running = 0;
+  }
+  c.flags[0] = running;
+  c.flags[1] = upd;
+  if (c.use_graph_cond) {
+    if (fin == FIN_NORM) cudaGraphSetConditional(c.h_update, (unsigned)upd);
+    if (fin == FIN_NORM || fin == FIN_RESID) cudaGraphSetConditional(c.h_loop, (unsigned)running);
+  }
+}
+
 static inline int nblk(long long n, int bt) { return (int)((n + bt - 1) / bt); }
+
+cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st) {
+  k_finalize<<<nsys, FIN_BT, 0, st>>>(c, fin, nbx, nv, nsys);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st) {
   const int nb = nblk(Ve, 256);

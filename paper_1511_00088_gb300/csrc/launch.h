@@ -30,6 +30,9 @@ cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int la
                               cudaStream_t st, const DsArgs &a);
 
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+// k_finalize over the partials of the kernel just launched: nbx blocks per
+// system group, nv values per system
+cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st);
 cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 
 cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st);

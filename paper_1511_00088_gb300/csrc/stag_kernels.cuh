@@ -97,15 +97,11 @@ struct SysState {
 
 struct Ctl {
   SysState *st;          // [nsys]
-  double *partials;      // [nsys][NVMAX][pstride]   one per block
-  double *partials2;     // [nsys][NVMAX][cstride]   one per chunk of RED_CHUNK blocks
-  unsigned *grp_ticket;  // [ngroups]
-  unsigned *chunk_ticket;  // [ngroups][cstride]
-  unsigned *all_ticket;  // [1]
+  double *partials;      // [nsys][NVMAX][pstride]   one per block of the reducing kernel
+  unsigned *all_ticket;  // [1] finalize blocks done
   int *flags;            // [0] any system running, [1] any reliable update due,
                          // [2] passes of the norm kernel this solve, [3] cap on [2]
   int pstride;           // partial slots per (system, value)
-  int cstride;           // chunk slots per (system, value) = ceil(pstride / RED_CHUNK)
   int use_graph_cond;    // call cudaGraphSetConditional on the handles below
   cudaGraphConditionalHandle h_loop, h_update;
 };
@@ -448,30 +444,20 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
   }
 }
 
-// Called by every thread of every block after it accumulated val[k][v] for
-// the NS systems j0 + k of its group.  bx/nbx: block index / count within the
-// group.  Two-level and deterministic: each block publishes one partial per
-// (system, value); the last block to finish within a chunk of RED_CHUNK
-// consecutive blocks sums the chunk in block order; the last chunk to finish
-// sums the chunk sums in chunk order and runs the finalisers.  Fixed summation
-// trees throughout, so reruns are bit-identical; no serial tail longer than a
-// few loads per lane.
-constexpr int RED_CHUNK = 64;
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// T = float: the per-thread values and the 32-lane tree are FP32 (GB300 runs
-// FP64 at a small fraction of the FP32 rate); every sum across warps and
-// blocks is FP64.  T = double: FP64 throughout (FP64 kernels).
+// Reductions, in two stages (both with fixed summation order, so reruns are
+// bit-identical):
+//  1. block_partials, in every block of a reducing kernel: a 32-lane tree
+//     (FP32 when T = float: GB300 runs FP64 at a small fraction of the FP32
+//     rate), then the warp sums in FP64 in warp order; thread 0 stores one
+//     FP64 partial per (system, value) with a plain store -- no fence, no
+//     atomic, so no block waits on a memory round trip;
+//  2. k_finalize, launched right after on the same stream: one block per
+//     system sums that system's partials in block order (FP64), runs the
+//     system's scalar logic, and the last finalize block to finish publishes
+//     the loop/update flags and the graph conditions.
 template <int NS, int NV, class T>
-__device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, T (&val)[NS][NV], int grp,
-                                                    int ngroups, int j0, int nsys, int bx, int nbx) {
+__device__ __forceinline__ void block_partials(const Ctl &c, T (&val)[NS][NV], int j0, int nsys, int bx) {
   __shared__ double red[32][NS * NV];
-  __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
@@ -481,99 +467,19 @@ __device__ __forceinline__ void reduce_and_finalize(const Ctl &c, int fin, T (&v
       if (lane == 0) red[warp][k * NV + v] = (double)w;
     }
   __syncthreads();
-  const int chunk = bx / RED_CHUNK;
-  const int nchunks = (nbx + RED_CHUNK - 1) / RED_CHUNK;
-  const int csize = min(RED_CHUNK, nbx - chunk * RED_CHUNK);
-  if (threadIdx.x == 0) {
-    // one thread publishes the block's partials, then takes a ticket of its chunk
-    for (int kv = 0; kv < NS * NV; ++kv) {
-      const int k = kv / NV, v = kv % NV;
-      double s = 0.0;
-      for (int w = 0; w < nwarp; ++w) s += red[w][kv];
-      if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = s;
-    }
-    __threadfence();
-    const unsigned t = atomicAdd(c.chunk_ticket + (long long)grp * c.cstride + chunk, 1u);
-    am_last = (t == (unsigned)(csize - 1));
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // level 1: this chunk's partials, in block order
-  for (int kv = warp; kv < NS * NV; kv += nwarp) {
-    const int k = kv / NV, v = kv % NV;
-    if (j0 + k >= nsys) continue;
-    const double *p = c.partials + ((long long)(j0 + k) * NVMAX + v) * c.pstride + chunk * RED_CHUNK;
-    double s = (lane < csize ? __ldcg(p + lane) : 0.0) + (lane + 32 < csize ? __ldcg(p + lane + 32) : 0.0);
-    s = warp_sum(s);
-    if (lane == 0) c.partials2[((long long)(j0 + k) * NVMAX + v) * c.cstride + chunk] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    c.chunk_ticket[(long long)grp * c.cstride + chunk] = 0u;
-    __threadfence();
-    const unsigned t = atomicAdd(c.grp_ticket + grp, 1u);
-    am_last = (t == (unsigned)(nchunks - 1));
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // level 2: the chunk sums, in chunk order
-  __shared__ double sums[NS][NVMAX];
-  for (int kv = warp; kv < NS * NV; kv += nwarp) {
-    const int k = kv / NV, v = kv % NV;
+  if (threadIdx.x < NS * NV) {
+    const int kv = threadIdx.x, k = kv / NV, v = kv % NV;
     double s = 0.0;
-    if (j0 + k < nsys) {
-      const double *p = c.partials2 + ((long long)(j0 + k) * NVMAX + v) * c.cstride;
-      for (int i = lane; i < nchunks; i += 32) s += __ldcg(p + i);
-    }
-    s = warp_sum(s);
-    if (lane == 0) sums[k][v] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    c.grp_ticket[grp] = 0u;
-    for (int k = 0; k < NS; ++k) {
-      const int j = j0 + k;
-      if (j >= nsys) continue;
-      // only systems that took part are finalised (see sys_gate)
-      bool part;
-      {
-        const int done = __ldcg(&c.st[j].done), upd = __ldcg(&c.st[j].update);
-        if (fin == FIN_INIT) part = true;
-        else if (fin == FIN_RESID) part = ((done == 0 || done == 3) && upd != 0);
-        else part = (done == 0);
-      }
-      if (part) finalize_system(c, fin, j, sums[k]);
-    }
-    __threadfence();
-    const unsigned t = atomicAdd(c.all_ticket, 1u);
-    if (t == (unsigned)(ngroups - 1)) {
-      *c.all_ticket = 0u;
-      __threadfence();
-      int running = 0, upd = 0;
-      for (int j = 0; j < nsys; ++j) {
-        const int done = __ldcg(&c.st[j].done);
-        if (done == 0 || done == 3) {
-          running = 1;
-          if (__ldcg(&c.st[j].update)) upd = 1;
-        }
-      }
-      if (fin == FIN_NORM) {
-        // absolute bound on the number of loop passes, whatever the state says
-        const int passes = c.flags[2] + 1;
-        c.flags[2] = passes;
-        if (passes > c.flags[3]) running = 0;
-      }
-      c.flags[0] = running;
-      c.flags[1] = upd;
-      if (c.use_graph_cond) {
-        if (fin == FIN_NORM) cudaGraphSetConditional(c.h_update, (unsigned)upd);
-        if (fin == FIN_NORM || fin == FIN_RESID) cudaGraphSetConditional(c.h_loop, (unsigned)running);
-      }
-    }
+    for (int w = 0; w < nwarp; ++w) s += red[w][kv];
+    if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = s;
   }
 }
+
+constexpr int FIN_BT = 1024;
+
+// grid = nsys blocks of FIN_BT threads; block j reduces system j's nv partial
+// arrays of nbx entries each (defined in blas.cu)
+__global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys);
 
 // ---------------------------------------------------------------------------
 // the half operator with fused epilogues
@@ -604,7 +510,7 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   const Geom g = a.g;
   const int Ve = g.Ve;
   const int G = a.ngroups;
-  const int grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
+  const int grp = blockIdx.x % G, bx = blockIdx.x / G;
   const int j0 = grp * NS;
   const int lane = LANES == 1 ? 0 : (int)(threadIdx.x % LANES);
   const int s = bx * (BT / LANES) + (int)(threadIdx.x / LANES);
@@ -769,7 +675,7 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   }
 
   if (EPI == EPI_CG_K1 || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
-    if (a.ctl.st != nullptr) reduce_and_finalize<NS, NV>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+    if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx);
   }
 }
 
@@ -805,7 +711,7 @@ __global__ void __launch_bounds__(BT) k_accum_x(const BlasArgs a) {
 template <int VP, int RP, int NS, int BT>
 __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
   typedef typename Tr<RP>::R R;
-  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G, nbx = gridDim.x / G;
+  const int G = a.ngroups, grp = blockIdx.x % G, bx = blockIdx.x / G;
   const int j0 = grp * NS, Ve = a.Ve;
   const int s = bx * BT + threadIdx.x;
   double part[NS][2];
@@ -839,7 +745,7 @@ __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
     part[k][0] = bb;
     part[k][1] = (double)rr;
   }
-  reduce_and_finalize<NS, 2>(a.ctl, a.fin, part, grp, G, j0, a.nsys, bx, nbx);
+  block_partials<NS, 2>(a.ctl, part, j0, a.nsys, bx);
 }
 
 // ---------------------------------------------------------------------------
