@@ -5,18 +5,19 @@
 //
 // CG driver.  Per iteration, for every running system j (all on the GPU, no
 // host round trip), two kernels:
-//   K1  p = r + beta p_old formed in the neighbour gather; t = D_oe p;
-//       |t|^2 and |p|^2 -> alpha = rho / (4 m_j^2 |p|^2 + |t|^2)
-//       (= <p, A p>, as D_eo^dag = -D_oe)                  (FP64 reduction)
+//   K1  t = D_oe r + beta t_old (= D_oe p for p = r + beta p_old);
+//       |t|^2, with |p|^2 = rho + 2 beta Re<r,p_old> + beta^2 |p_old|^2 ->
+//       alpha = rho / (4 m_j^2 |p|^2 + |t|^2) (= <p, A p>, D_eo^dag = -D_oe)
+//       (with FP16/BF16 Krylov vectors: p formed in the gather, |p|^2 reduced)
 //   K2  p = r + beta p_old at the centre (stored); A p = 4 m^2 p - D_eo t;
-//       r -= alpha A p; x_lo += alpha p; |r|^2 -> beta; reliable-update and
-//       convergence triggers                              (FP64 reduction)
+//       r -= alpha A p; x_lo += alpha p; |r|^2, Re<r,p> -> beta; reliable-
+//       update and convergence triggers                   (FP64 reduction)
 //   if a reliable update is pending (a conditional graph node at the end of
 //   every SOLVE_UNROLL iterations):
-//   K4  x64 += x_lo,  x_lo = 0
+//   K4  x64 += x_lo,  x_lo = 0;  t = D_oe p (restarts the t recurrence)
 //   K5  t64 = D_oe x64                                    (FP64)
 //   K6  r = b - (4 m^2 x64 - D_eo t64) in FP64, stored at the residual's
-//       precision; ||r||^2 in FP64 -> true residual, convergence, beta
+//       precision; ||r||^2, Re<r,p> in FP64 -> true residual, convergence, beta
 // The iterations sit in the body of a CUDA-graph WHILE node whose condition
 // the last block of K2 / K6 sets ("any system still running"); the update
 // kernels sit in an IF node set by K2.  One graph launch runs the whole solve.
@@ -458,6 +459,7 @@ BlasArgs blas_base(stag_ctx *c, const Ctl &ctl) {
   b.x = w.x.arg();
   b.b = w.b64.arg();
   b.x64 = w.x64.arg();
+  b.t = w.t.arg();
   b.nsys = w.nsys;
   b.ngroups = w.G;
   b.ctl = ctl;
@@ -477,21 +479,30 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.gate = GATE_RUNNING;
   a.aux = w.r.arg();
   a.xlo = w.x.arg();
-  // K1: t = D_oe (r + beta p_old); |t|^2, |p|^2 -> alpha
+  // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2) -> alpha
   a.par_out = 1;
-  a.in = w.p.arg();
+  a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
   a.out = w.t.arg();
-  a.fin = FIN_ALPHA;
   const int nbx = ds_blocks(c->Ve, w.lanes);
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nbx * w.G, s, a));
-  CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s));
+  if (w.VP == w.RP) {
+    // t = D_oe r + beta t_old: one gathered vector; |p|^2 from the scalar recurrence
+    a.out = w.t.arg();
+    a.fin = FIN_ALPHA_R;
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1R, w.lanes, nbx * w.G, s, a));
+    CK(launch_finalize(ctl, FIN_ALPHA_R, nbx, 1, w.nsys, s));
+  } else {
+    // FP16/BF16 Krylov vectors: no t recurrence (its rounding would accumulate)
+    a.fin = FIN_ALPHA;
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nbx * w.G, s, a));
+    CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s));
+  }
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.fin = FIN_NORM;
   CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes, nbx * w.G, s, a));
-  CK(launch_finalize(ctl, FIN_NORM, nbx, 1, w.nsys, s));
+  CK(launch_finalize(ctl, FIN_NORM, nbx, 2, w.nsys, s));
   return STAG_OK;
 }
 
@@ -502,6 +513,23 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   b.gate = GATE_UPDATE;
   b.fin = FIN_NONE;
   CK(launch_accum_x(w.RP, w.NS, w.nbx_bl * w.G, s, b));
+  if (w.VP == w.RP) {
+    // restart the t recurrence from t = D_oe p exactly
+    const void *lo = nullptr;
+    CKS(links_for(c, w.prec, &lo));
+    DsArgs q = ds_base(c);
+    q.links = lo;
+    q.nsys = w.nsys;
+    q.ngroups = w.G;
+    q.ctl = ctl;
+    q.gate = GATE_UPDATE;
+    q.fin = FIN_NONE;
+    q.par_out = 1;
+    q.in = w.p.arg();
+    q.out = w.t.arg();
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_PLAIN, w.lanes, ds_blocks(c->Ve, w.lanes) * w.G, s,
+                     q));
+  }
   DsArgs a = ds_base(c);
   a.links = c->links64.p;
   a.nsys = w.nsys;
@@ -519,8 +547,9 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.aux = w.b64.arg();
   a.out = w.r.arg();
   a.fin = FIN_RESID;
+  if (w.VP == w.RP) a.dir = w.p.arg();  // Re<r_true, p> for the |p|^2 recurrence
   CK(launch_dslash(P64, 0, P64, w.RP, w.NS64, EPI_RESID, w.lanes64, ds_blocks(c->Ve, w.lanes64) * w.G64, s, a));
-  CK(launch_finalize(ctl, FIN_RESID, ds_blocks(c->Ve, w.lanes64), 1, w.nsys, s));
+  CK(launch_finalize(ctl, FIN_RESID, ds_blocks(c->Ve, w.lanes64), 2, w.nsys, s));
   return STAG_OK;
 }
 
@@ -948,17 +977,18 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   a.gate = GATE_NONE;
   a.fin = FIN_NONE;
   a.par_out = 1;
-  a.in = w.p.arg();
+  const int k1 = (w.VP == w.RP) ? EPI_CG_K1R : EPI_CG_K1;
+  a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
   a.aux = w.r.arg();
   a.out = w.t.arg();
   const int nb = ds_blocks(c->Ve, w.lanes) * w.G;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -970,7 +1000,8 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
     const double lb = (double)cplx_bytes(w.prec) * (w.recon ? 6 : 9);
     const double vb = (double)cplx_bytes(w.VP) * 3 + ((w.VP == P16 || w.VP == PBF) ? 4 : 0);
     const double rb = (double)cplx_bytes(w.RP) * 3;
-    // links once; p_old and r once (through cache); t written once
+    // links once; gathered vectors once (through cache); t read (recurrence) or
+    // p_old read (gather form) and t written
     *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * (2.0 * vb + rb));
   }
   return STAG_OK;

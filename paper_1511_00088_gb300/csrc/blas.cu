@@ -48,27 +48,29 @@ cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const B
 // grid = nsys blocks of FIN_BT threads; block j reduces system j's nv partial
 // arrays of nbx entries each
 __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys) {
-  __shared__ double red[FIN_BT / 32][NVMAX];
+  __shared__ double red[NVMAX][FIN_BT / 32];
   __shared__ double sums[NVMAX];
   const int j = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // balanced fixed-order trees: few dependent FP64 additions
   for (int v = 0; v < nv; ++v) {
     const double *p = c.partials + ((long long)j * NVMAX + v) * c.pstride;
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = threadIdx.x;
-    for (; i + FIN_BT < nbx; i += 2 * FIN_BT) {
+    for (; i + 3 * FIN_BT < nbx; i += 4 * FIN_BT) {
       s0 += p[i];
       s1 += p[i + FIN_BT];
+      s2 += p[i + 2 * FIN_BT];
+      s3 += p[i + 3 * FIN_BT];
     }
-    if (i < nbx) s0 += p[i];
-    const double w = warp_sum(s0 + s1);
-    if (lane == 0) red[warp][v] = w;
+    for (; i < nbx; i += FIN_BT) s0 += p[i];
+    const double w = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) red[v][warp] = w;
   }
   __syncthreads();
-  if (threadIdx.x < nv) {
-    double s = 0.0;
-    for (int w = 0; w < FIN_BT / 32; ++w) s += red[w][threadIdx.x];
-    sums[threadIdx.x] = s;
+  if (warp < nv) {
+    const double w = warp_sum(red[warp][lane]);
+    if (lane == 0) sums[warp] = w;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;

@@ -17,4 +17,5 @@
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_PLAIN)          \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_MDAGM)          \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_CG_K1)          \
+  STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_CG_K1R)         \
   STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_CG_K2)

@@ -81,11 +81,13 @@ struct SysState {
   double rho;       // ||r||^2 of the iterated residual
   double pAp;       // <p, A p>
   double alpha, beta;
-  double rmax;      // ||r|| at the last reliable update (FP64)
   double true_res;  // ||b - A x|| / ||b|| at the last reliable update
   double tol;       // stop when ||b - A x|| / ||b|| <= tol
   double delta;     // reliable update when ||r|| < delta * rmax (0: only at tol)
   double rho_prev;  // ||r||^2 one iteration back (beta after a reliable update)
+  double pnorm2;    // |p|^2 of the current direction
+  double rp;        // Re <r, p> of the current residual and direction
+  double rmax2;     // ||r||^2 at the last reliable update
   int maxiter;
   int iter;
   int done;         // 0 running, 3 stopped until the pending FP64 check, 1 converged,
@@ -107,8 +109,8 @@ struct Ctl {
 };
 
 enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_UPDATE = 2 };
-enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_CG_K1 = 2, EPI_RESID = 3, EPI_CG_K2 = 4 };
-enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_NORM = 2, FIN_RESID = 3, FIN_INIT = 4 };
+enum { EPI_PLAIN = 0, EPI_MDAGM = 1, EPI_CG_K1 = 2, EPI_RESID = 3, EPI_CG_K2 = 4, EPI_CG_K1R = 5 };
+enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_NORM = 2, FIN_RESID = 3, FIN_INIT = 4, FIN_ALPHA_R = 5 };
 
 struct DsArgs {
   Geom g;
@@ -120,6 +122,8 @@ struct DsArgs {
   VecArg out;            // output (EPI_RESID: the reduced-precision residual)
   VecArg aux;            // EPI_RESID: the source b (FP64); EPI_CG_K1/K2: the residual r
   VecArg xlo;            // EPI_CG_K2: the partial solution x_lo (read and written)
+  VecArg dir;            // EPI_RESID: the direction p at the residual's precision for
+                         // Re<r, p> (v == nullptr: not reduced)
   double m4_single;      // 4 m^2 when ctl == nullptr
   int nsys, ngroups;
   Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
@@ -128,7 +132,7 @@ struct DsArgs {
 
 struct BlasArgs {
   int Ve;
-  VecArg p, r, x, b, x64;   // meanings per kernel
+  VecArg p, r, x, b, x64, t;   // meanings per kernel
   int nsys, ngroups;
   Ctl ctl;
   int gate, fin;
@@ -368,21 +372,27 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
 }
 
 // Per-system scalar logic of the CG iteration, run once per reduction by the
-// thread that holds the FP64 sums.
-//   FIN_ALPHA: alpha = rho / <p, Ap> with <p, Ap> = 4 m^2 |p|^2 + |D_oe p|^2
-//              (breakdown if it is not positive and finite)
-//   FIN_NORM:  rho_new = ||r||^2; beta = rho_new / rho; a reliable update becomes
-//              pending when ||r|| < delta r_max; when ||r|| <= tol ||b|| or the
-//              iteration cap is reached the system stops (done = 3) until the
-//              pending FP64 recomputation decides
-//   FIN_RESID: true residual from the FP64 recomputation: converged, capped, or
-//              continue with rho = ||r_true||^2 and beta = rho / rho_prev
-//   FIN_INIT:  ||b||^2 and ||r||^2 of the starting residual
+// thread that holds the FP64 sums.  Written with few dependent FP64 operations
+// (GB300's FP64 pipe is narrow and long-latency): squares are compared
+// instead of norms, and square roots are taken only for the reported residual.
+//   FIN_ALPHA:   sums |t|^2, |p|^2 of the new direction p = r + beta p_old:
+//                alpha = rho / (4 m^2 |p|^2 + |t|^2)  (= <p, A p>, D_eo^dag = -D_oe)
+//   FIN_ALPHA_R: as FIN_ALPHA with |p|^2 = rho + 2 beta Re<r, p_old> + beta^2 |p_old|^2
+//                (the first kernel then only reduces |t|^2)
+//   FIN_NORM:    sums |r|^2, Re<r, p>: beta = rho_new / rho; a reliable update
+//                becomes pending when |r| < delta r_max; when |r| <= tol |b| or
+//                the iteration cap is reached the system stops (done = 3) until
+//                the pending FP64 recomputation decides
+//   FIN_RESID:   sums of the FP64 recomputation |b - A x|^2, Re<r, p>: converged,
+//                capped, or continue with rho = |r_true|^2, beta = rho / rho_prev
+//   FIN_INIT:    |b|^2 and |r|^2 of the starting residual
+// (breakdown, done = -5, on a non-positive <p, A p> or a non-finite sum)
 __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, const double *sum) {
   SysState &s = c.st[j];
-  if (fin == FIN_ALPHA) {
-    // <p, (4m^2 - D_eo D_oe) p> = 4 m^2 |p|^2 + |D_oe p|^2  (D_eo^dag = -D_oe)
-    const double pAp = s.m4 * sum[1] + sum[0];
+  if (fin == FIN_ALPHA || fin == FIN_ALPHA_R) {
+    const double p2 = (fin == FIN_ALPHA) ? sum[1] : s.rho + s.beta * (2.0 * s.rp + s.beta * s.pnorm2);
+    const double pAp = s.m4 * p2 + sum[0];
+    s.pnorm2 = p2;
     s.pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       s.done = -5;
@@ -396,14 +406,14 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
       s.done = -5;
       return;
     }
+    s.rp = sum[1];
     s.rho_prev = s.rho;
     s.beta = rr / s.rho;
     s.rho = rr;
-    const double rn = sqrt(rr);
-    if (rn <= s.tol * sqrt(s.bnorm2) || s.iter >= s.maxiter) {
+    if (rr <= s.tol * s.tol * s.bnorm2 || s.iter >= s.maxiter) {
       s.update = 1;
       s.done = 3;
-    } else if (rn < s.delta * s.rmax) {
+    } else if (rr < s.delta * s.delta * s.rmax2) {
       s.update = 1;
     }
   } else if (fin == FIN_RESID) {
@@ -414,9 +424,9 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
       s.done = -5;
       return;
     }
-    s.true_res = sqrt(rr / s.bnorm2);
-    s.rmax = sqrt(rr);
-    if (s.true_res <= s.tol) {
+    s.rmax2 = rr;
+    s.rp = sum[1];
+    if (rr <= s.tol * s.tol * s.bnorm2) {
       s.done = 1;
     } else if (s.iter >= s.maxiter) {
       s.done = 2;
@@ -425,11 +435,14 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
       s.beta = rr / s.rho_prev;
       s.rho = rr;
     }
+    s.true_res = sqrt(rr / s.bnorm2);
   } else if (fin == FIN_INIT) {
     s.bnorm2 = sum[0];
     s.rho = sum[1];
     s.rho_prev = sum[1];
-    s.rmax = sqrt(sum[0]);
+    s.rmax2 = sum[0];
+    s.pnorm2 = 0.0;
+    s.rp = 0.0;
     s.iter = 0;
     s.update = 0;
     s.n_updates = 0;
@@ -446,32 +459,32 @@ __device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, co
 
 // Reductions, in two stages (both with fixed summation order, so reruns are
 // bit-identical):
-//  1. block_partials, in every block of a reducing kernel: a 32-lane tree
-//     (FP32 when T = float: GB300 runs FP64 at a small fraction of the FP32
-//     rate), then the warp sums in FP64 in warp order; thread 0 stores one
-//     FP64 partial per (system, value) with a plain store -- no fence, no
-//     atomic, so no block waits on a memory round trip;
+//  1. block_partials, in every block of a reducing kernel: a 32-lane tree and
+//     the warp sums in warp order, in FP32 when T = float (GB300 runs FP64 at
+//     a small fraction of the FP32 rate, with long latency); the block sum is
+//     stored as one FP64 partial per (system, value) with a plain store -- no
+//     fence, no atomic, so no block waits on a memory round trip;
 //  2. k_finalize, launched right after on the same stream: one block per
 //     system sums that system's partials in block order (FP64), runs the
 //     system's scalar logic, and the last finalize block to finish publishes
 //     the loop/update flags and the graph conditions.
 template <int NS, int NV, class T>
 __device__ __forceinline__ void block_partials(const Ctl &c, T (&val)[NS][NV], int j0, int nsys, int bx) {
-  __shared__ double red[32][NS * NV];
+  __shared__ T red[32][NS * NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T w = warp_sum(val[k][v]);
-      if (lane == 0) red[warp][k * NV + v] = (double)w;
+      if (lane == 0) red[warp][k * NV + v] = w;
     }
   __syncthreads();
   if (threadIdx.x < NS * NV) {
     const int kv = threadIdx.x, k = kv / NV, v = kv % NV;
-    double s = 0.0;
+    T s = 0;
     for (int w = 0; w < nwarp; ++w) s += red[w][kv];
-    if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = s;
+    if (j0 + k < nsys) c.partials[((long long)(j0 + k) * NVMAX + v) * c.pstride + bx] = (double)s;
   }
 }
 
@@ -496,16 +509,20 @@ __global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys);
 // EPI_MDAGM:  out = m4 center - D in
 // EPI_CG_K1:  t = D_oe p_new with p_new = r + beta p_old formed in the gather;
 //             |t|^2 and |p_new|^2 per system -> FIN_ALPHA
+// EPI_CG_K1R: t = D_oe r + beta t_old (the same t by linearity, one gathered
+//             vector instead of two); |t|^2 per system -> FIN_ALPHA_R
 // EPI_CG_K2:  p_new (again, at the centre), Ap = m4 p_new - D_eo t,
-//             r -= alpha Ap, x_lo += alpha p_new; |r|^2 per system -> FIN_NORM
+//             r -= alpha Ap, x_lo += alpha p_new; |r|^2, Re<r,p> -> FIN_NORM
 // EPI_RESID:  (FP64) out = b - (m4 x - D in), stored at the output precision,
-//             plus ||b - A x||^2 per system (FP64) -> FIN_RESID
+//             plus ||b - A x||^2 and Re<r, p> per system (FP64) -> FIN_RESID
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
 __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
   constexpr bool XPAY_GATHER = (EPI == EPI_CG_K1);  // fold r + beta p into the neighbour gather
-  constexpr int NV = (EPI == EPI_CG_K1) ? 2 : 1;     // reduction values per system
+  // reduction values per system: K1 |t|^2, |p|^2; K2 |r|^2, Re<r,p>; RESID
+  // |b - A x|^2, Re<r,p>; K1R |t|^2
+  constexpr int NV = (EPI == EPI_CG_K1 || EPI == EPI_CG_K2 || EPI == EPI_RESID) ? 2 : 1;
   constexpr int DPL = 4 / LANES;  // directions per lane
   const Geom g = a.g;
   const int Ve = g.Ve;
@@ -629,11 +646,15 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
             rv[i] -= alpha * ap;
             xv[i] += alpha * cv[i];
           }
-          R q = 0;
+          R q = 0, rp = 0;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            if (c % LANES == lane) q += rv[2 * c] * rv[2 * c] + rv[2 * c + 1] * rv[2 * c + 1];
+            if (c % LANES == lane) {
+              q += rv[2 * c] * rv[2 * c] + rv[2 * c + 1] * rv[2 * c + 1];
+              rp += rv[2 * c] * cv[2 * c] + rv[2 * c + 1] * cv[2 * c + 1];
+            }
           part[k][0] += q;
+          part[k][1] += rp;
         }
         if (LANES > 1) __syncwarp();  // every lane has read the site before any lane writes it
         if (valid) {
@@ -641,6 +662,23 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
           store_site_share<RP, LANES>(a.aux, j, s, Ve, lane, rv);
           store_site_share<RP, LANES>(a.xlo, j, s, Ve, lane, xv);
         }
+        continue;
+      }
+      if (EPI == EPI_CG_K1R) {
+        // t = D_oe r + beta t_old (= D_oe (r + beta p_old) by linearity); |t|^2
+        R tv[6];
+        if (valid) {
+          load_vec_rw<VP>(a.out, j, s, Ve, tv);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) tv[i] = acc[k][i] + beta[k] * tv[i];
+          R q = 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c % LANES == lane) q += tv[2 * c] * tv[2 * c] + tv[2 * c + 1] * tv[2 * c + 1];
+          part[k][0] += q;
+        }
+        if (LANES > 1) __syncwarp();
+        if (valid) store_site_share<VP, LANES>(a.out, j, s, Ve, lane, tv);
         continue;
       }
       if (!valid) continue;
@@ -666,15 +704,24 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         load_vec<P64>(a.aux, j, s, Ve, bv);
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
+        R pv[6] = {0, 0, 0, 0, 0, 0};
+        if (a.dir.v != nullptr) load_vec<OP>(a.dir, j, s, Ve, pv);
+        // Re<r, p> of the residual as it will be stored (rounded to OP)
+        typename Tr<OP>::R orr[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) orr[i] = (typename Tr<OP>::R)o[i];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (c % LANES == lane) part[k][0] += o[2 * c] * o[2 * c] + o[2 * c + 1] * o[2 * c + 1];
+          if (c % LANES == lane) {
+            part[k][0] += o[2 * c] * o[2 * c] + o[2 * c + 1] * o[2 * c + 1];
+            part[k][1] += (R)orr[2 * c] * pv[2 * c] + (R)orr[2 * c + 1] * pv[2 * c + 1];
+          }
       }
       store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
     }
   }
 
-  if (EPI == EPI_CG_K1 || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
+  if (EPI == EPI_CG_K1 || EPI == EPI_CG_K1R || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
     if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx);
   }
 }
@@ -738,8 +785,9 @@ __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
     R rr = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) rr += rr_[i] * rr_[i];
-    // p_old = 0 and beta = 0: the first iteration forms p = r itself
+    // p_old = 0, t_old = 0 and beta = 0: the first iteration forms p = r itself
     store_vec<VP>(a.p, j, s, Ve, z);
+    store_vec<VP>(a.t, j, s, Ve, z);
     store_vec<RP>(a.x, j, s, Ve, z);
     store_vec<P64>(a.x64, j, s, Ve, z64);
     part[k][0] = bb;
