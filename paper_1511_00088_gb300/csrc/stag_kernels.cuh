@@ -515,8 +515,13 @@ __global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys);
 //             r -= alpha Ap, x_lo += alpha p_new; |r|^2, Re<r,p> -> FIN_NORM
 // EPI_RESID:  (FP64) out = b - (m4 x - D in), stored at the output precision,
 //             plus ||b - A x||^2 and Re<r, p> per system (FP64) -> FIN_RESID
+// __launch_bounds__(BT, 1): without the minimum-blocks argument ptxas caps the
+// registers and serialises the loads of the hops; with it, the loads of a
+// thread's directions are all in flight together (measured: 27 us instead of
+// 34 us for D_oe at 20^3 x 64, FP32).
+// (The FP64 kernels are bound by GB300's FP64 pipe and keep 4 blocks per SM.)
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
-__global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
+__global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a) {
   typedef typename Tr<LP>::R R;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
   constexpr bool XPAY_GATHER = (EPI == EPI_CG_K1);  // fold r + beta p into the neighbour gather
@@ -524,6 +529,11 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   // |b - A x|^2, Re<r,p>; K1R |t|^2
   constexpr int NV = (EPI == EPI_CG_K1 || EPI == EPI_CG_K2 || EPI == EPI_RESID) ? 2 : 1;
   constexpr int DPL = 4 / LANES;  // directions per lane
+  // number of centre vectors the epilogue reads at this site
+  constexpr int NC = (EPI == EPI_CG_K2) ? 3 : (EPI == EPI_RESID) ? 3 : (EPI == EPI_MDAGM || EPI == EPI_CG_K1R) ? 1 : 0;
+  // one system: every load of the site is issued before any arithmetic (one
+  // memory round trip per thread); several systems: per direction
+  constexpr bool HOIST = (NS == 1);
   const Geom g = a.g;
   const int Ve = g.Ve;
   const int G = a.ngroups;
@@ -555,10 +565,30 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) acc[k][i] = 0;
 
+  // centre vectors of the single-system epilogue, loaded up front (HOIST)
+  R cpre[NC > 0 ? NC : 1][6];
   const int P = a.par_out;
   if (any && valid) {
+    if (HOIST && NC > 0) {
+      if (EPI == EPI_CG_K2) {
+        load_vec_rw<VP>(a.center, j0, s, Ve, cpre[0]);
+        load_vec_rw<RP>(a.aux, j0, s, Ve, cpre[NC > 1 ? 1 : 0]);
+        load_vec_rw<RP>(a.xlo, j0, s, Ve, cpre[NC > 2 ? 2 : 0]);
+      } else if (EPI == EPI_RESID) {
+        load_vec<P64>(a.center, j0, s, Ve, cpre[0]);
+        load_vec<P64>(a.aux, j0, s, Ve, cpre[NC > 1 ? 1 : 0]);
+        if (a.dir.v != nullptr) load_vec<OP>(a.dir, j0, s, Ve, cpre[NC > 2 ? 2 : 0]);
+      } else if (EPI == EPI_CG_K1R) {
+        load_vec_rw<VP>(a.out, j0, s, Ve, cpre[0]);
+      } else {  // EPI_MDAGM
+        load_vec<VP>(a.center, j0, s, Ve, cpre[0]);
+      }
+    }
     int x[4];
     site_coords(g, P, s, x);
+    // the two hops of each direction of this lane: neighbour sites and signs
+    int sf[DPL], sb[DPL];
+    R bf[DPL], bb[DPL];
 #pragma unroll
     for (int dd = 0; dd < DPL; ++dd) {
       const int mu = lane * DPL + dd;
@@ -573,42 +603,83 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
       int xb[4] = {x[0], x[1], x[2], x[3]};
       xf[mu] = (xm + 1 == Lmu) ? 0 : xm + 1;
       xb[mu] = (xm == 0) ? Lmu - 1 : xm - 1;
-      const int sf = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
-      const int sb = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
-      R bf = eta, bb = eta;
+      sf[dd] = cb_of(g, xf[0], xf[1], xf[2], xf[3]);
+      sb[dd] = cb_of(g, xb[0], xb[1], xb[2], xb[3]);
+      bf[dd] = eta;
+      bb[dd] = eta;
       if (mu == 3 && g.ap) {
-        if (xm == g.L3 - 1) bf = -bf;
-        if (xm == 0) bb = -bb;
+        if (xm == g.L3 - 1) bf[dd] = -bf[dd];
+        if (xm == 0) bb[dd] = -bb[dd];
       }
-      R uf[18], ub[18];
-      load_link<LP, RECON>(a.links, Ve, P, mu, s, uf);
-      load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb, ub);
+    }
+    if (HOIST) {
+      R uf[DPL][18], ub[DPL][18], vf[DPL][6], vb[DPL][6];
 #pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        if (!act[k]) continue;
-        R vf[6], vb[6];
-        load_vec<VP>(a.in, k + j0, sf, Ve, vf);
-        load_vec<VP>(a.in, k + j0, sb, Ve, vb);
-        if (XPAY_GATHER) {  // the operator acts on p_new = r + beta p_old, formed here
+      for (int dd = 0; dd < DPL; ++dd) {
+        const int mu = lane * DPL + dd;
+        load_link<LP, RECON>(a.links, Ve, P, mu, s, uf[dd]);
+        load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb[dd], ub[dd]);
+        load_vec<VP>(a.in, j0, sf[dd], Ve, vf[dd]);
+        load_vec<VP>(a.in, j0, sb[dd], Ve, vb[dd]);
+      }
+      if (XPAY_GATHER) {  // the operator acts on p_new = r + beta p_old, formed here
+#pragma unroll
+        for (int dd = 0; dd < DPL; ++dd) {
           R rf[6], rb[6];
-          load_vec<RP>(a.aux, k + j0, sf, Ve, rf);
-          load_vec<RP>(a.aux, k + j0, sb, Ve, rb);
+          load_vec<RP>(a.aux, j0, sf[dd], Ve, rf);
+          load_vec<RP>(a.aux, j0, sb[dd], Ve, rb);
 #pragma unroll
           for (int i = 0; i < 6; ++i) {
-            vf[i] = rf[i] + beta[k] * vf[i];
-            vb[i] = rb[i] + beta[k] * vb[i];
+            vf[dd][i] = rf[i] + beta[0] * vf[dd][i];
+            vb[dd][i] = rb[i] + beta[0] * vb[dd][i];
           }
           // |p_new|^2 over the even sites: each even site is the forward-x
           // neighbour of exactly one odd site, so count it there
-          if (mu == 0 && NV > 1) {
+          if (lane * DPL + dd == 0 && NV > 1) {
             R q = 0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) q += vf[i] * vf[i];
-            part[k][NV - 1] += q;
+            for (int i = 0; i < 6; ++i) q += vf[dd][i] * vf[dd][i];
+            part[0][NV - 1] += q;
           }
         }
-        mv_acc(uf, vf, bf, acc[k]);
-        mvdag_acc(ub, vb, -bb, acc[k]);
+      }
+#pragma unroll
+      for (int dd = 0; dd < DPL; ++dd) {
+        mv_acc(uf[dd], vf[dd], bf[dd], acc[0]);
+        mvdag_acc(ub[dd], vb[dd], -bb[dd], acc[0]);
+      }
+    } else {
+#pragma unroll
+      for (int dd = 0; dd < DPL; ++dd) {
+        const int mu = lane * DPL + dd;
+        R uf[18], ub[18];
+        load_link<LP, RECON>(a.links, Ve, P, mu, s, uf);
+        load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb[dd], ub);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (!act[k]) continue;
+          R vf[6], vb[6];
+          load_vec<VP>(a.in, k + j0, sf[dd], Ve, vf);
+          load_vec<VP>(a.in, k + j0, sb[dd], Ve, vb);
+          if (XPAY_GATHER) {
+            R rf[6], rb[6];
+            load_vec<RP>(a.aux, k + j0, sf[dd], Ve, rf);
+            load_vec<RP>(a.aux, k + j0, sb[dd], Ve, rb);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              vf[i] = rf[i] + beta[k] * vf[i];
+              vb[i] = rb[i] + beta[k] * vb[i];
+            }
+            if (mu == 0 && NV > 1) {
+              R q = 0;
+#pragma unroll
+              for (int i = 0; i < 6; ++i) q += vf[i] * vf[i];
+              part[k][NV - 1] += q;
+            }
+          }
+          mv_acc(uf, vf, bf[dd], acc[k]);
+          mvdag_acc(ub, vb, -bb[dd], acc[k]);
+        }
       }
     }
   }
@@ -622,23 +693,33 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
   }
 
   // The epilogue loop runs on every lane (act[] is uniform across the block) so
-  // that the warp barrier of the fused direction update is reached by all
-  // lanes; per-lane work is predicated on `valid`.
+  // that the warp barriers are reached by all lanes; per-lane work is
+  // predicated on `valid`.
   if (any) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (!act[k]) continue;
       const int j = k + j0;
       if (EPI == EPI_CG_K2) {
-        // p_new = r + beta p_old at this site (as the first kernel formed it at the
-        // neighbours); Ap = 4 m^2 p_new - D_eo t; r -= alpha Ap; x_lo += alpha p_new;
-        // p_new, r, x_lo stored; |r|^2 reduced.  Ap itself is never stored.
+        // p_new = r + beta p_old at this site (the first kernel formed the same at
+        // the neighbours); Ap = 4 m^2 p_new - D_eo t; r -= alpha Ap; x_lo += alpha
+        // p_new; p_new, r, x_lo stored; |r|^2 and Re<r, p_new> reduced.  Ap itself
+        // is never stored.
         R cv[6], rv[6], xv[6];
         const R alpha = (R)a.ctl.st[j].alpha;
         if (valid) {
-          load_vec_rw<VP>(a.center, j, s, Ve, cv);
-          load_vec_rw<RP>(a.aux, j, s, Ve, rv);
-          load_vec_rw<RP>(a.xlo, j, s, Ve, xv);
+          if (HOIST) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              cv[i] = cpre[0][i];
+              rv[i] = cpre[NC > 1 ? 1 : 0][i];
+              xv[i] = cpre[NC > 2 ? 2 : 0][i];
+            }
+          } else {
+            load_vec_rw<VP>(a.center, j, s, Ve, cv);
+            load_vec_rw<RP>(a.aux, j, s, Ve, rv);
+            load_vec_rw<RP>(a.xlo, j, s, Ve, xv);
+          }
 #pragma unroll
           for (int i = 0; i < 6; ++i) {
             cv[i] = rv[i] + beta[k] * cv[i];
@@ -668,7 +749,12 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         // t = D_oe r + beta t_old (= D_oe (r + beta p_old) by linearity); |t|^2
         R tv[6];
         if (valid) {
-          load_vec_rw<VP>(a.out, j, s, Ve, tv);
+          if (HOIST) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) tv[i] = cpre[0][i];
+          } else {
+            load_vec_rw<VP>(a.out, j, s, Ve, tv);
+          }
 #pragma unroll
           for (int i = 0; i < 6; ++i) tv[i] = acc[k][i] + beta[k] * tv[i];
           R q = 0;
@@ -695,17 +781,31 @@ __global__ void __launch_bounds__(BT) k_dslash(const DsArgs a) {
         }
       } else if (EPI == EPI_MDAGM) {
         R cv[6];
-        load_vec<VP>(a.center, j, s, Ve, cv);
+        if (HOIST) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) cv[i] = cpre[0][i];
+        } else {
+          load_vec<VP>(a.center, j, s, Ve, cv);
+        }
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
       } else {  // EPI_RESID (R = double)
         R xx[6], bv[6];
-        load_vec<P64>(a.center, j, s, Ve, xx);
-        load_vec<P64>(a.aux, j, s, Ve, bv);
+        R pv[6] = {0, 0, 0, 0, 0, 0};
+        if (HOIST) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            xx[i] = cpre[0][i];
+            bv[i] = cpre[NC > 1 ? 1 : 0][i];
+            if (a.dir.v != nullptr) pv[i] = cpre[NC > 2 ? 2 : 0][i];
+          }
+        } else {
+          load_vec<P64>(a.center, j, s, Ve, xx);
+          load_vec<P64>(a.aux, j, s, Ve, bv);
+          if (a.dir.v != nullptr) load_vec<OP>(a.dir, j, s, Ve, pv);
+        }
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = bv[i] - (m4[k] * xx[i] - acc[k][i]);
-        R pv[6] = {0, 0, 0, 0, 0, 0};
-        if (a.dir.v != nullptr) load_vec<OP>(a.dir, j, s, Ve, pv);
         // Re<r, p> of the residual as it will be stored (rounded to OP)
         typename Tr<OP>::R orr[6];
 #pragma unroll
