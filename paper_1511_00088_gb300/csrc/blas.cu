@@ -47,53 +47,72 @@ cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const B
 
 // grid = nsys blocks of FIN_BT threads; block j reduces system j's nv partial
 // arrays of nbx entries each
+// Written for latency: every global load is issued before any result is
+// used (partials, the system's state), the state is updated in registers and
+// stored once, and with a single system there is no cross-block ticket and no
+// fence (the next kernel in the stream sees the stores).
 __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys) {
+  constexpr int PER = 4;  // partials per thread per value in flight at once
   __shared__ double red[NVMAX][FIN_BT / 32];
   __shared__ double sums[NVMAX];
   const int j = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // balanced fixed-order trees: few dependent FP64 additions
-  for (int v = 0; v < nv; ++v) {
-    const double *p = c.partials + ((long long)j * NVMAX + v) * c.pstride;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int i = threadIdx.x;
-    for (; i + 3 * FIN_BT < nbx; i += 4 * FIN_BT) {
-      s0 += p[i];
-      s1 += p[i + FIN_BT];
-      s2 += p[i + 2 * FIN_BT];
-      s3 += p[i + 3 * FIN_BT];
-    }
-    for (; i < nbx; i += FIN_BT) s0 += p[i];
-    const double w = warp_sum((s0 + s1) + (s2 + s3));
+  SysState st;
+  if (threadIdx.x == 0) st = c.st[j];
+  double acc[NVMAX];
+#pragma unroll
+  for (int v = 0; v < NVMAX; ++v) acc[v] = 0.0;
+  for (int base = 0; base < nbx; base += PER * FIN_BT) {
+    double x[NVMAX][PER];
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int i = base + u * FIN_BT + threadIdx.x;
+        x[v][u] = (v < nv && i < nbx) ? c.partials[((long long)j * NVMAX + v) * c.pstride + i] : 0.0;
+      }
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v) acc[v] += (x[v][0] + x[v][1]) + (x[v][2] + x[v][3]);
+  }
+#pragma unroll
+  for (int v = 0; v < NVMAX; ++v) {
+    const double w = warp_sum(acc[v]);
     if (lane == 0) red[v][warp] = w;
   }
   __syncthreads();
-  if (warp < nv) {
+  if (warp < NVMAX) {
     const double w = warp_sum(red[warp][lane]);
     if (lane == 0) sums[warp] = w;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   {
-    const int done = c.st[j].done, upd = c.st[j].update;
     bool part;
     if (fin == FIN_INIT) part = true;
-    else if (fin == FIN_RESID) part = ((done == 0 || done == 3) && upd != 0);
-    else part = (done == 0);
-    if (part) finalize_system(c, fin, j, sums);
-  }
-  __threadfence();
-  const unsigned t = atomicAdd(c.all_ticket, 1u);
-  if (t != (unsigned)(nsys - 1)) return;
-  *c.all_ticket = 0u;
-  __threadfence();
-  int running = 0, upd = 0;
-  for (int q = 0; q < nsys; ++q) {
-    const int done = __ldcg(&c.st[q].done);
-    if (done == 0 || done == 3) {
-      running = 1;
-      if (__ldcg(&c.st[q].update)) upd = 1;
+    else if (fin == FIN_RESID) part = ((st.done == 0 || st.done == 3) && st.update != 0);
+    else part = (st.done == 0);
+    if (part && fin != FIN_NONE) {
+      finalize_system(st, fin, sums);
+      c.st[j] = st;
     }
+  }
+  int running = 0, upd = 0;
+  if (nsys > 1) {
+    __threadfence();
+    const unsigned t = atomicAdd(c.all_ticket, 1u);
+    if (t != (unsigned)(nsys - 1)) return;
+    *c.all_ticket = 0u;
+    __threadfence();
+    for (int q = 0; q < nsys; ++q) {
+      const int done = __ldcg(&c.st[q].done);
+      if (done == 0 || done == 3) {
+        running = 1;
+        if (__ldcg(&c.st[q].update)) upd = 1;
+      }
+    }
+  } else {
+    running = (st.done == 0 || st.done == 3) ? 1 : 0;
+    upd = running && st.update;
   }
   if (fin == FIN_NORM) {
     // absolute bound on the number of loop passes, whatever the state says

@@ -387,8 +387,7 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
 //                capped, or continue with rho = |r_true|^2, beta = rho / rho_prev
 //   FIN_INIT:    |b|^2 and |r|^2 of the starting residual
 // (breakdown, done = -5, on a non-positive <p, A p> or a non-finite sum)
-__device__ __forceinline__ void finalize_system(const Ctl &c, int fin, int j, const double *sum) {
-  SysState &s = c.st[j];
+__device__ __forceinline__ void finalize_system(SysState &s, int fin, const double *sum) {
   if (fin == FIN_ALPHA || fin == FIN_ALPHA_R) {
     const double p2 = (fin == FIN_ALPHA) ? sum[1] : s.rho + s.beta * (2.0 * s.rp + s.beta * s.pnorm2);
     const double pAp = s.m4 * p2 + sum[0];
