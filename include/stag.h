@@ -186,6 +186,21 @@ int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_upd
 int stag_mdagm_dot_noalloc(stag_ctx *ctx, double mass, const double *in_even, double *tmp_odd,
                            double *out_even, double *dot);
 
+/*
+ * Fermion force of the action S = phi^dag A^{-1} phi, A = 4 m^2 - D_eo D_oe,
+ * given the solution x_even = A^{-1} phi (e.g. from stag_cg_solve in FP64).
+ * The derivative of S with respect to the gauge field (the molecular-dynamics
+ * force of the HYP-smeared staggered quarks of Sec. 3, computed on the
+ * one-link field the operator uses):
+ *   grad_links [4][V][3][3][2] (may be NULL): dS/dRe U + i dS/dIm U per link
+ *              (the torch convention), = K^dag with dS = Re Tr(K dU);
+ *   lie_force  [4][V][8] (may be NULL): f_a = Re Tr(i T_a U K), T_a =
+ *              lambda_a / 2, the derivative along U -> exp(i w T_a) U.
+ * One FP64 half operator (Y = D_oe X) plus one pass over the links; FP64.
+ * Host or device pointers.  Errors: STAG_ERR_ARG, STAG_ERR_STATE, _CUDA.
+ */
+int stag_force(stag_ctx *ctx, const double *x_even, double *grad_links, double *lie_force);
+
 /* Message of the last error on this context ("" when none). */
 const char *stag_last_error(const stag_ctx *ctx);
 

@@ -948,6 +948,58 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
 }
 
+int stag_force(stag_ctx *c, const double *x_even, double *grad_links, double *lie_force) {
+  if (!c) return STAG_ERR_ARG;
+  if (!x_even) return arg_err(c, "NULL solution vector");
+  if (!grad_links && !lie_force) return arg_err(c, "no output requested");
+  CK(cudaSetDevice(c->device));
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  const int Ve = c->Ve;
+  const double2 *d = nullptr;
+  CKS(vec_in(c, x_even, c->stage_in, 0, &d));
+  CK(c->api_a.ensure(P64, 1, Ve));
+  CK(c->api_b.ensure(P64, 1, Ve));
+  CK(launch_pack_vec(P64, d, c->api_a.arg(), 0, Ve, c->stream));
+  // Y = D_oe X (FP64)
+  int lanes = 1;
+  CKS(tune_lanes(c, P64, 0, P64, 1, 1, 1, c->links64.p, c->api_a.arg(), c->api_b.arg(), &lanes));
+  DsArgs a = ds_base(c);
+  a.links = c->links64.p;
+  a.nsys = 1;
+  a.ngroups = 1;
+  a.ctl = no_ctl();
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.par_out = 1;
+  a.in = c->api_a.arg();
+  a.out = c->api_b.arg();
+  CK(launch_dslash(P64, 0, P64, P64, 1, EPI_PLAIN, lanes, ds_blocks(Ve, lanes), c->stream, a));
+  const size_t gbytes = sizeof(double) * 18ull * 4ull * c->V, lbytes = sizeof(double) * 8ull * 4ull * c->V;
+  double2 *gdev = nullptr;
+  double *ldev = nullptr;
+  const bool g_host = grad_links && !is_device_ptr(grad_links);
+  const bool l_host = lie_force && !is_device_ptr(lie_force);
+  size_t off = 0;
+  if (g_host) off += gbytes;
+  if (l_host) off += lbytes;
+  if (off) CK(c->stage_out.ensure(off));
+  off = 0;
+  if (grad_links) {
+    gdev = g_host ? (double2 *)c->stage_out.p : (double2 *)grad_links;
+    if (g_host) off += gbytes;
+  }
+  if (lie_force) ldev = l_host ? (double *)((char *)c->stage_out.p + off) : lie_force;
+  CK(launch_force(c->g, (const double2 *)c->api_a.data.p, (const double2 *)c->api_b.data.p, c->links64.p, gdev, ldev,
+                  c->stream));
+  if (g_host) CK(cudaMemcpyAsync(grad_links, gdev, gbytes, cudaMemcpyDeviceToHost, c->stream));
+  if (l_host) CK(cudaMemcpyAsync(lie_force, ldev, lbytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
+}
+
 int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updates, double *true_res) {
   if (!c || c->last_nsys <= 0 || sys < 0 || sys >= c->last_nsys) return STAG_ERR_ARG;
   const SysState *hs = (const SysState *)c->w.h_st.p;

@@ -44,4 +44,9 @@ cudaError_t launch_pack_links(int LP, int recon, const double2 *src, void *dst, 
 cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
                               cudaStream_t st);
 
+// k_force over all 4 V links (force.cu): X even, Y = D_oe X odd (device SoA,
+// FP64); grad [4][V][3][3] complex and/or lie [4][V][8] (either may be null)
+cudaError_t launch_force(Geom g, const double2 *X, const double2 *Y, const void *links64, double2 *grad,
+                         double *lie, cudaStream_t st);
+
 }  // namespace stag

@@ -72,6 +72,7 @@ def load():
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
+            "stag_force": (I, [P, P, P, P]),
             "stag_last_error": (ctypes.c_char_p, [P]),
             "stag_status_string": (ctypes.c_char_p, [I]),
             "stag_abi_version": (I, []),
@@ -178,6 +179,11 @@ def stag_mdagm_dot_noalloc(ctx, mass, in_even, tmp_odd, out_even, dot=None):
                                          None if dot is None else _ptr(dot))
 
 
+def stag_force(ctx, x_even, grad_links=None, lie_force=None):
+    return load().stag_force(ctx, _ptr(x_even), None if grad_links is None else _ptr(grad_links),
+                             None if lie_force is None else _ptr(lie_force))
+
+
 def stag_last_error(ctx):
     return load().stag_last_error(ctx).decode()
 
@@ -276,6 +282,24 @@ class Context:
         st, it, nu, tr = stag_solve_stats(self.h, sys)
         self._check(st)
         return it, nu, tr
+
+    def force(self, x_even, grad=True, lie=False):
+        """(grad_links (4, V, 3, 3) complex128 or None, lie (4, V, 8) float64 or None)
+        for S = phi^dag A^{-1} phi at the solution x_even = A^{-1} phi."""
+        try:
+            import torch
+            dev = x_even.device if isinstance(x_even, torch.Tensor) else None
+        except ImportError:  # pragma: no cover
+            dev = None
+        if dev is not None:
+            import torch
+            g = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device=dev) if grad else None
+            f = torch.empty((4, self.V, 8), dtype=torch.float64, device=dev) if lie else None
+        else:
+            g = np.empty((4, self.V, 3, 3), np.complex128) if grad else None
+            f = np.empty((4, self.V, 8), np.float64) if lie else None
+        self._check(stag_force(self.h, x_even, g, f))
+        return g, f
 
     def time_dslash(self, precision=STAG_FP32, nlaunch=50):
         st, ms, by = stag_time_dslash(self.h, precision, nlaunch)
