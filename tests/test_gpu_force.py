@@ -70,13 +70,13 @@ def test_force_central_differences_16x32():
     ctx = stag.Context(L)
     try:
         ctx.links_upload(Ud)
-        xs, _, _, _ = ctx.cg_solve([phid], [m], tol=1e-13, precision=stag.STAG_FP64)
+        xs, _, _, _ = ctx.cg_solve([phid], [m], tol=1e-12, precision=stag.STAG_FP64)
         _, f = ctx.force(xs[0], grad=False, lie=True)
         f = f.cpu().numpy()
 
         def action():
             ctx.links_upload(Ud)
-            x, _, _, _ = ctx.cg_solve([phid], [m], tol=1e-13, precision=stag.STAG_FP32)
+            x, _, _, _ = ctx.cg_solve([phid], [m], tol=1e-12, precision=stag.STAG_FP32)
             x = x[0]
             Ax = ctx.mdagm(x, m, stag.STAG_FP64)
             return float(2 * torch.real(torch.vdot(phid.reshape(-1), x.reshape(-1)))
