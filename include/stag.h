@@ -156,6 +156,29 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
 int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_launch,
                      double *bytes_per_launch);
 
+/* One lattice of a ragged batch: the arguments of stag_cg_solve for ctx. */
+typedef struct stag_solve_desc {
+  stag_ctx *ctx;
+  const double *const *src; /* nrhs sources */
+  int nrhs;
+  const double *masses; /* nmass masses */
+  int nmass;
+  double *const *x;  /* nrhs * nmass solutions, slot r * nmass + k */
+  int *iters;        /* nrhs * nmass, may be NULL */
+  double *true_res;  /* nrhs * nmass, may be NULL */
+} stag_solve_desc;
+
+/*
+ * Solve several lattices of different sizes (one context each, same device)
+ * together: every lattice's solve loop is a branch of one CUDA graph, so the
+ * GPU runs them concurrently (Sec. 3 workloads batched; one graph launch for
+ * the whole ragged batch).  The first context's stream orders the batch.
+ * tol, maxiter and precision as in stag_cg_solve, shared by all lattices.
+ * Returns the worst status over the lattices (an error, else
+ * STAG_NOT_CONVERGED, else STAG_OK); per-system results in each entry.
+ */
+int stag_cg_solve_ragged(const stag_solve_desc *descs, int ndesc, double tol, int maxiter, int precision);
+
 /*
  * Statistics of system `sys` (0 <= sys < nrhs * nmass) of the most recent
  * stag_cg_solve on this context: iterations, FP64 reliable updates (the

@@ -127,12 +127,14 @@ struct Work {
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
   cudaGraphConditionalHandle h_loop = 0, h_update = 0;
+  unsigned long long gen = 0;  // bumped whenever captured kernels may hold stale arguments
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
     graph_tried = false;
+    ++gen;
   }
   ~Work() { drop_graph(); }
 };
@@ -170,6 +172,7 @@ struct stag_ctx {
   DevBuf defect;
   Work w;
   int last_nsys = 0;  // systems of the most recent solve (stats in w.h_st)
+  unsigned long long id = 0;  // process-unique, never reused
 };
 
 namespace {
@@ -575,21 +578,23 @@ int build_graph(stag_ctx *c) {
   return st;
 }
 
-int build_graph_inner(stag_ctx *c) {
+// Add one context's solve loop to graph g: a WHILE node (condition: any
+// system still running) whose body holds SOLVE_UNROLL iterations and an IF
+// node (condition: a reliable update pending) around the update kernels.
+// The conditional handles are stored in the context's workspace, where the
+// captured kernels read them.
+int add_solve_loop(stag_ctx *c, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *out) {
   Work &w = c->w;
-  w.graph_tried = true;
   if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   if (!c->cap2) CK(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
-  cudaGraph_t g = nullptr;
-  CK(cudaGraphCreate(&g, 0));
-  w.graph = g;
   CK(cudaGraphConditionalHandleCreate(&w.h_loop, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
   wp.conditional.handle = w.h_loop;
   wp.conditional.type = cudaGraphCondTypeWhile;
   wp.conditional.size = 1;
   cudaGraphNode_t wn;
-  CK(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+  CK(cudaGraphAddNode(&wn, g, deps, nullptr, ndeps, &wp));
+  if (out) *out = wn;
   cudaGraph_t body = wp.conditional.phGraph_out[0];
   CK(cudaGraphConditionalHandleCreate(&w.h_update, body, 0, cudaGraphCondAssignDefault));
   const Ctl ctl = work_ctl(c, true);
@@ -603,11 +608,11 @@ int build_graph_inner(stag_ctx *c) {
     return st;
   }
   cudaStreamCaptureStatus cs;
-  const cudaGraphNode_t *deps = nullptr;
-  size_t ndeps = 0;
+  const cudaGraphNode_t *cdeps = nullptr;
+  size_t ncdeps = 0;
   cudaGraph_t capg = nullptr;
-  CK(cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &capg, &deps, nullptr, &ndeps));
-  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  CK(cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &capg, &cdeps, nullptr, &ncdeps));
+  std::vector<cudaGraphNode_t> dv(cdeps, cdeps + ncdeps);
   cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
   ip.conditional.handle = w.h_update;
   ip.conditional.type = cudaGraphCondTypeIf;
@@ -627,18 +632,29 @@ int build_graph_inner(stag_ctx *c) {
     cudaGraph_t tmp;
     CK(cudaStreamEndCapture(c->cap, &tmp));
   }
+  return STAG_OK;
+}
+
+int build_graph_inner(stag_ctx *c) {
+  Work &w = c->w;
+  w.graph_tried = true;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  w.graph = g;
+  CKS(add_solve_loop(c, g, nullptr, 0, nullptr));
   CK(cudaGraphInstantiate(&w.exec, g, 0));
   return STAG_OK;
 }
 
-int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
-               double tol, int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
+// Solve phases (shared by the single and the ragged solve)
+// stage: sources, per-system parameters and the CG start, on c->stream
+int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass, double tol,
+                int maxiter, int prec) {
   const int nsys = nrhs * nmass;
   CKS(work_prepare(c, nsys, prec));
   Work &w = c->w;
   const void *lo = nullptr;
   CKS(links_for(c, w.prec, &lo));
-
   // sources -> b64 (FP64 internal layout)
   for (int r = 0; r < nrhs; ++r) {
     const double2 *d = nullptr;
@@ -674,7 +690,53 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     CK(launch_cg_init(w.VP, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
     CK(launch_finalize(ctl0, FIN_INIT, w.nbx_bl, 2, nsys, c->stream));
   }
+  return STAG_OK;
+}
 
+// run the staged solve eagerly (no graph), polling the device flag
+int solve_eager(stag_ctx *c, int maxiter) {
+  Work &w = c->w;
+  const Ctl ctl = work_ctl(c, false);
+  int *hf = (int *)w.h_flags.p;
+  const int passes_per_poll = 4;  // the same sequence as the graph body, polled every 4 passes
+  for (long long it = 0; it <= (long long)maxiter + 2 * SOLVE_UNROLL * passes_per_poll;
+       it += SOLVE_UNROLL * passes_per_poll) {
+    for (int i = 0; i < passes_per_poll; ++i) {
+      for (int u = 0; u < SOLVE_UNROLL; ++u) CKS(enqueue_main(c, c->stream, ctl));
+      CKS(enqueue_update(c, c->stream, ctl));
+    }
+    CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hf[0] == 0) break;
+  }
+  return STAG_OK;
+}
+
+// copy the solutions and statistics out; the solve's status
+int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[]) {
+  Work &w = c->w;
+  const int nsys = w.nsys;
+  SysState *hs = (SysState *)w.h_st.p;
+  CK(cudaMemcpyAsync(hs, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
+  for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
+  CK(cudaStreamSynchronize(c->stream));
+  c->last_nsys = nsys;
+  int status = STAG_OK;
+  for (int j = 0; j < nsys; ++j) {
+    if (iters) iters[j] = hs[j].iter;
+    if (true_res) true_res[j] = hs[j].true_res;
+    if (hs[j].done == -5) status = STAG_ERR_BREAKDOWN;
+    else if (hs[j].done != 1 && status == STAG_OK) status = STAG_NOT_CONVERGED;
+  }
+  if (status == STAG_ERR_BREAKDOWN) c->err = "CG breakdown: <p, A p> not positive or a non-finite residual";
+  else if (status == STAG_NOT_CONVERGED) c->err = "iteration cap reached before the tolerance";
+  return status;
+}
+
+int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+               double tol, int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
+  CKS(solve_stage(c, src, nrhs, masses, nmass, tol, maxiter, prec));
+  Work &w = c->w;
   bool ran = false;
   if (c->use_graph) {
     if (!w.graph_tried) {
@@ -691,36 +753,8 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
       ran = true;
     }
   }
-  if (!ran) {
-    const Ctl ctl = work_ctl(c, false);
-    int *hf = (int *)w.h_flags.p;
-    const int passes_per_poll = 4;  // the same sequence as the graph body, polled every 4 passes
-    for (long long it = 0; it <= (long long)maxiter + 2 * SOLVE_UNROLL * passes_per_poll;
-         it += SOLVE_UNROLL * passes_per_poll) {
-      for (int i = 0; i < passes_per_poll; ++i) {
-        for (int u = 0; u < SOLVE_UNROLL; ++u) CKS(enqueue_main(c, c->stream, ctl));
-        CKS(enqueue_update(c, c->stream, ctl));
-      }
-      CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
-      CK(cudaStreamSynchronize(c->stream));
-      if (hf[0] == 0) break;
-    }
-  }
-  CK(cudaMemcpyAsync(hs, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
-  for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
-  CK(cudaStreamSynchronize(c->stream));
-
-  c->last_nsys = nsys;
-  int status = STAG_OK;
-  for (int j = 0; j < nsys; ++j) {
-    if (iters) iters[j] = hs[j].iter;
-    if (true_res) true_res[j] = hs[j].true_res;
-    if (hs[j].done == -5) status = STAG_ERR_BREAKDOWN;
-    else if (hs[j].done != 1 && status == STAG_OK) status = STAG_NOT_CONVERGED;
-  }
-  if (status == STAG_ERR_BREAKDOWN) c->err = "CG breakdown: <p, A p> not positive or a non-finite residual";
-  else if (status == STAG_NOT_CONVERGED) c->err = "iteration cap reached before the tolerance";
-  return status;
+  if (!ran) CKS(solve_eager(c, maxiter));
+  return solve_finish(c, x, iters, true_res);
 }
 
 // operator calls of the ABI: the FP64 input is rounded to `prec` (per-site
@@ -783,6 +817,116 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// ragged batch: several contexts (lattices of different sizes) in one graph
+// ---------------------------------------------------------------------------
+struct RaggedGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+std::map<std::vector<unsigned long long>, RaggedGraph> g_ragged;
+std::mutex g_ragged_mu;
+unsigned long long g_next_ctx_id = 1;
+
+void ragged_forget(unsigned long long id) {
+  std::lock_guard<std::mutex> lk(g_ragged_mu);
+  for (auto it = g_ragged.begin(); it != g_ragged.end();) {
+    bool has = false;
+    for (size_t k = 0; k < it->first.size(); k += 2) has |= it->first[k] == id;
+    if (has) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      if (it->second.graph) cudaGraphDestroy(it->second.graph);
+      it = g_ragged.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+int ragged_impl(const stag_solve_desc *d, int n, double tol, int maxiter, int prec) {
+  stag_ctx *c0 = d[0].ctx;
+  std::vector<cudaStream_t> saved(n);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = d[i].ctx->stream;
+    d[i].ctx->stream = c0->stream;  // one stream orders the whole batch
+  }
+  struct Restore {
+    const stag_solve_desc *d;
+    int n;
+    std::vector<cudaStream_t> &s;
+    ~Restore() {
+      for (int i = 0; i < n; ++i) d[i].ctx->stream = s[i];
+    }
+  } restore{d, n, saved};
+  for (int i = 0; i < n; ++i) {
+    stag_ctx *c = d[i].ctx;
+    CKS(solve_stage(c, d[i].src, d[i].nrhs, d[i].masses, d[i].nmass, tol, maxiter, prec));
+  }
+  bool graph_ok = true;
+  for (int i = 0; i < n; ++i) graph_ok &= d[i].ctx->use_graph;
+  bool ran = false;
+  if (graph_ok) {
+    std::vector<unsigned long long> key;
+    for (int i = 0; i < n; ++i) {
+      key.push_back(d[i].ctx->id);
+      key.push_back(d[i].ctx->w.gen);
+    }
+    cudaGraphExec_t exec = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_ragged_mu);
+      auto it = g_ragged.find(key);
+      if (it != g_ragged.end()) exec = it->second.exec;
+    }
+    if (!exec) {
+      RaggedGraph rg;
+      stag_ctx *c = c0;
+      CK(cudaGraphCreate(&rg.graph, 0));
+      int st = STAG_OK;
+      for (int i = 0; i < n && st == STAG_OK; ++i) {
+        st = add_solve_loop(d[i].ctx, rg.graph, nullptr, 0, nullptr);
+        if (st != STAG_OK) {
+          cudaStreamCaptureStatus cs;
+          cudaGraph_t tmp = nullptr;
+          stag_ctx *ci = d[i].ctx;
+          if (ci->cap2 && cudaStreamIsCapturing(ci->cap2, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(ci->cap2, &tmp);
+          if (ci->cap && cudaStreamIsCapturing(ci->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(ci->cap, &tmp);
+          cudaGetLastError();
+        }
+      }
+      if (st == STAG_OK && cudaGraphInstantiate(&rg.exec, rg.graph, 0) == cudaSuccess) {
+        exec = rg.exec;
+        std::lock_guard<std::mutex> lk(g_ragged_mu);
+        g_ragged[key] = rg;
+      } else {
+        cudaGetLastError();
+        if (rg.graph) cudaGraphDestroy(rg.graph);
+      }
+    }
+    if (exec) {
+      stag_ctx *c = c0;
+      CK(cudaGraphLaunch(exec, c0->stream));
+      ran = true;
+    }
+  }
+  if (!ran)
+    for (int i = 0; i < n; ++i) CKS(solve_eager(d[i].ctx, maxiter));
+  int status = STAG_OK;
+  for (int i = 0; i < n; ++i) {
+    const int st = solve_finish(d[i].ctx, d[i].x, d[i].iters, d[i].true_res);
+    if (st < 0 || (st == STAG_NOT_CONVERGED && status == STAG_OK)) status = st;
+  }
+  if (status != STAG_OK) {
+    for (int i = 0; i < n; ++i)
+      if (!d[i].ctx->err.empty()) {
+        c0->err = d[i].ctx->err;
+        break;
+      }
+  }
+  return status;
+}
 
 // Internal accessors used by noalloc.cu (not part of the C ABI).
 namespace stag {
@@ -848,6 +992,10 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   c->g.dLxh = make_fastdiv((unsigned)(dims[0] / 2));
   c->g.dL1 = make_fastdiv((unsigned)dims[1]);
   c->g.dL2 = make_fastdiv((unsigned)dims[2]);
+  {
+    std::lock_guard<std::mutex> lk(g_ragged_mu);
+    c->id = g_next_ctx_id++;
+  }
   const char *eager = getenv("STAG_EAGER");
   c->use_graph = !(eager && eager[0] == '1');
   cudaError_t e = cudaGetDevice(&c->device);
@@ -864,6 +1012,7 @@ int stag_destroy(stag_ctx *c) {
   if (!c) return STAG_OK;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  ragged_forget(c->id);
   c->w.drop_graph();
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
@@ -946,6 +1095,34 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_cg_solve_ragged(const stag_solve_desc *descs, int ndesc, double tol, int maxiter, int precision) {
+  if (!descs || ndesc < 1) return STAG_ERR_ARG;
+  stag_ctx *c = descs[0].ctx;
+  if (!c) return STAG_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0)) return arg_err(c, "tol must be in (0, 1)");
+  if (maxiter < 1) return arg_err(c, "maxiter must be >= 1");
+  {
+    int a_, b_, c_;
+    if (!solver_precs(precision, &a_, &b_, &c_)) return arg_err(c, "bad solver precision");
+  }
+  for (int i = 0; i < ndesc; ++i) {
+    const stag_solve_desc &d = descs[i];
+    if (!d.ctx || !d.src || !d.masses || !d.x || d.nrhs < 1 || d.nmass < 1) return arg_err(c, "bad ragged entry");
+    if ((long long)d.nrhs * d.nmass > 4096) return arg_err(c, "at most 4096 systems per lattice");
+    if (d.ctx->device != c->device) return arg_err(c, "all lattices of a ragged batch must be on one device");
+    for (int q = 0; q < i; ++q)
+      if (descs[q].ctx == d.ctx) return arg_err(c, "a context appears twice in a ragged batch");
+    for (int r = 0; r < d.nrhs; ++r)
+      if (!d.src[r]) return arg_err(c, "NULL source");
+    for (int j = 0; j < d.nrhs * d.nmass; ++j)
+      if (!d.x[j]) return arg_err(c, "NULL solution buffer");
+    for (int k = 0; k < d.nmass; ++k)
+      if (!std::isfinite(d.masses[k])) return arg_err(c, "non-finite mass");
+  }
+  CK(cudaSetDevice(c->device));
+  return ragged_impl(descs, ndesc, tol, maxiter, precision);
 }
 
 int stag_force(stag_ctx *c, const double *x_even, double *grad_links, double *lie_force) {

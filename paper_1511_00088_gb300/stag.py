@@ -39,6 +39,13 @@ _lib = None
 _lock = threading.Lock()
 
 
+class SolveDesc(ctypes.Structure):
+    """struct stag_solve_desc: one lattice of a ragged batch."""
+    _fields_ = [("ctx", ctypes.c_void_p), ("src", ctypes.POINTER(ctypes.c_void_p)), ("nrhs", ctypes.c_int),
+                ("masses", ctypes.c_void_p), ("nmass", ctypes.c_int), ("x", ctypes.POINTER(ctypes.c_void_p)),
+                ("iters", ctypes.c_void_p), ("true_res", ctypes.c_void_p)]
+
+
 class StagError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -73,6 +80,7 @@ def load():
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_force": (I, [P, P, P, P]),
+            "stag_cg_solve_ragged": (I, [ctypes.POINTER(SolveDesc), I, D, I, I]),
             "stag_last_error": (ctypes.c_char_p, [P]),
             "stag_status_string": (ctypes.c_char_p, [I]),
             "stag_abi_version": (I, []),
@@ -179,6 +187,28 @@ def stag_mdagm_dot_noalloc(ctx, mass, in_even, tmp_odd, out_even, dot=None):
                                          None if dot is None else _ptr(dot))
 
 
+def stag_cg_solve_ragged(entries, tol, maxiter, precision):
+    """entries: list of (ctx, srcs, masses, xs).  Returns (status, [iters], [true_res])."""
+    n = len(entries)
+    descs = (SolveDesc * n)()
+    keep = []
+    its, trs = [], []
+    for i, (ctx, srcs, masses, xs) in enumerate(entries):
+        sp = (ctypes.c_void_p * len(srcs))(*[_ptr(a) for a in srcs])
+        xp = (ctypes.c_void_p * len(xs))(*[_ptr(a) for a in xs])
+        m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+        it = np.zeros(len(xs), np.int32)
+        tr = np.zeros(len(xs), np.float64)
+        keep += [sp, xp, m]
+        its.append(it)
+        trs.append(tr)
+        descs[i] = SolveDesc(ctx, ctypes.cast(sp, ctypes.POINTER(ctypes.c_void_p)), len(srcs), m.ctypes.data,
+                             len(masses), ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), it.ctypes.data,
+                             tr.ctypes.data)
+    st = load().stag_cg_solve_ragged(descs, n, float(tol), int(maxiter), int(precision))
+    return st, its, trs
+
+
 def stag_force(ctx, x_even, grad_links=None, lie_force=None):
     return load().stag_force(ctx, _ptr(x_even), None if grad_links is None else _ptr(grad_links),
                              None if lie_force is None else _ptr(lie_force))
@@ -199,6 +229,21 @@ def stag_abi_version():
 # ---------------------------------------------------------------------------
 # a small object wrapper that raises on errors
 # ---------------------------------------------------------------------------
+def cg_solve_ragged(batch, tol=1e-10, maxiter=100000, precision=STAG_FP32, allow_not_converged=False):
+    """Solve several lattices in one graph launch.  batch: list of
+    (Context, srcs, masses).  Returns (list of xs per lattice, status, iters, true_res)."""
+    entries, outs = [], []
+    for ctx, srcs, masses in batch:
+        xs = [ctx._like(srcs[r]) for r in range(len(srcs)) for _ in masses]
+        outs.append(xs)
+        entries.append((ctx.h, srcs, masses, xs))
+    st, its, trs = stag_cg_solve_ragged(entries, tol, maxiter, precision)
+    ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
+    if st not in ok:
+        raise StagError(st, stag_last_error(batch[0][0].h))
+    return outs, st, its, trs
+
+
 class Context:
     """One lattice on the current CUDA device (see stag_create)."""
 
