@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--mass", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    ap.add_argument("--links", default="recon12", choices=["full", "recon12"],
+                    help="storage of the reduced-precision links (the FP64 copy is always full)")
     ap.add_argument("--no-extras", action="store_true",
                     help="profiling runs: skip the comparison solves, the e2e leg and the CPU baseline")
     return ap.parse_args()
@@ -67,8 +69,10 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(L, mass, tol, prec):
+def workload_config(L, mass, tol, prec, links="full"):
     return {
+        "link_storage": ("reconstruct-12 (rows 0, 1 stored; row 2 = conj(row0 x row1) in registers)"
+                         if links == "recon12" else "full 3x3") + f" at {prec.upper()}; FP64 copy full",
         "workload": f"{L[0]}^3x{L[3]} even-odd staggered CG, {prec.upper()} inner iteration, "
                     f"FP64 reliable updates (delta=0.1), m={mass}, 1 RHS, true residual {tol:g}"
         if L[0] == L[1] == L[2] else f"{L} staggered CG",
@@ -240,7 +244,7 @@ def run_ours(args):
     U = synth.random_links(L, 0.4, synth.seed_for(1, 1))
     b = synth.gaussian_vector(Ve, synth.seed_for(1, 2 + rank))
     stream = torch.cuda.current_stream()
-    ctx = stag.Context(L, stream=stream.cuda_stream)
+    ctx = stag.Context(L, recon12=(args.links == "recon12"), stream=stream.cuda_stream)
     ctx.links_upload(torch.from_numpy(U).cuda())
     bd = torch.from_numpy(b).cuda()
     xd = torch.empty_like(bd)
@@ -319,10 +323,11 @@ def run_ours(args):
     ms_ds, bytes_ds = ctx.time_dslash(prec, nlaunch=200)
     hbm, peak_kind = peaks()
     achieved = bytes_ds / (ms_ds * 1e-3) / 1e9
-    key = f"dslash_oe_{args.precision}_{'x'.join(map(str, L))}"
+    key = f"dslash_oe_{args.precision}{'_r12' if args.links == 'recon12' else ''}_{'x'.join(map(str, L))}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": ncu_traffic(key), "peak_source": peak_kind,
-            "kernel": f"k_dslash (D_oe, {args.precision}, 1 RHS)", "ms_per_launch": ms_ds,
+            "kernel": f"k_dslash CG K1: t = D_oe r + beta t ({args.precision}, links {args.links}, 1 RHS)",
+            "ms_per_launch": ms_ds,
             "algorithmic_bytes_per_launch": bytes_ds,
             "dslash_gflops": DSLASH_FLOP_PER_SITE * Ve / (ms_ds * 1e-3) / 1e9}
 
@@ -361,7 +366,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / PAPER_TX_CG_GFLOPS,
             "dtype": "f32" if args.precision == "fp32" else args.precision.replace("fp", "f"),
-            "data": "synthetic", "config": workload_config(L, args.mass, args.tol, args.precision),
+            "data": "synthetic", "config": workload_config(L, args.mass, args.tol, args.precision, args.links),
             "time_to_solution_ms": ms_step, "iters": iters[-1], "reliable_updates": updates[-1],
             "true_res": max(res),
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve,

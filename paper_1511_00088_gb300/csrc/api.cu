@@ -119,6 +119,7 @@ struct Work {
   int RP = P32;  // precision of the iterated residual r and partial solution x_lo
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
+  int lanes_k1 = 1, lanes_k2 = 1;  // lanes of the two CG kernels (tuned with their epilogues)
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
   DevBuf st, partials, tickets, flags;
@@ -317,6 +318,54 @@ void tune_cache_store(const TuneKey &k, int lanes) {
   fclose(f);
 }
 
+// Time both mappings of one instantiation: `a` holds the kernel's arguments.
+int tune_lanes_epi(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, const DsArgs &a, int *lanes_out) {
+  const char *force = getenv("STAG_LANES");
+  if (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) {
+    *lanes_out = force[0] - '0';
+    return STAG_OK;
+  }
+  const int G = a.ngroups;
+  const TuneKey key(LP, recon, VP, NS * 16 + EPI, G, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *lanes_out = it->second;
+      return STAG_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_l = 1;
+  for (int l = 1; l <= 2; ++l) {
+    const int nb = ds_blocks(c->Ve, l) * G;
+    for (int i = 0; i < 3; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI, l, nb, c->stream, a));
+    CK(cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < 10; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI, l, nb, c->stream, a));
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_l = l;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_l;
+    tune_cache_store(key, best_l);
+  }
+  *lanes_out = best_l;
+  return STAG_OK;
+}
+
 int tune_lanes(stag_ctx *c, int LP, int recon, int VP, int NS, int G, int nsys, const void *links, VecArg in,
                VecArg out, int *lanes_out) {
   const char *force = getenv("STAG_LANES");
@@ -379,6 +428,9 @@ int tune_lanes(stag_ctx *c, int LP, int recon, int VP, int NS, int G, int nsys, 
 // solver
 // ---------------------------------------------------------------------------
 
+Ctl work_ctl(stag_ctx *c, bool graph);
+DsArgs ds_base(stag_ctx *c);
+
 int work_prepare(stag_ctx *c, int nsys, int precision) {
   Work &w = c->w;
   int prec, VP, RP;
@@ -427,6 +479,27 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CKS(links_for(c, prec, &lo));
   CKS(tune_lanes(c, prec, recon, VP, w.NS, w.G, nsys, lo, w.p.arg(), w.t.arg(), &w.lanes));
   CKS(tune_lanes(c, P64, 0, P64, w.NS64, w.G64, nsys, c->links64.p, w.x64.arg(), w.t64.arg(), &w.lanes64));
+  {
+    // the two CG kernels with their own epilogues (state zeroed: alpha = beta = 0)
+    DsArgs a = ds_base(c);
+    a.links = lo;
+    a.nsys = nsys;
+    a.ngroups = w.G;
+    a.ctl = work_ctl(c, false);
+    a.gate = GATE_NONE;
+    a.fin = FIN_NONE;
+    a.aux = w.r.arg();
+    a.xlo = w.x.arg();
+    const bool rec = (VP == w.RP);
+    a.par_out = 1;
+    a.in = rec ? w.r.arg() : w.p.arg();
+    a.out = w.t.arg();
+    CKS(tune_lanes_epi(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, &w.lanes_k1));
+    a.par_out = 0;
+    a.in = w.t.arg();
+    a.center = w.p.arg();
+    CKS(tune_lanes_epi(c, prec, recon, VP, w.NS, EPI_CG_K2, a, &w.lanes_k2));
+  }
   return STAG_OK;
 }
 
@@ -486,17 +559,17 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.par_out = 1;
   a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
   a.out = w.t.arg();
-  const int nbx = ds_blocks(c->Ve, w.lanes);
+  const int nbx = ds_blocks(c->Ve, w.lanes_k1);
   if (w.VP == w.RP) {
     // t = D_oe r + beta t_old: one gathered vector; |p|^2 from the scalar recurrence
     a.out = w.t.arg();
     a.fin = FIN_ALPHA_R;
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1R, w.lanes, nbx * w.G, s, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1R, w.lanes_k1, nbx * w.G, s, a));
     CK(launch_finalize(ctl, FIN_ALPHA_R, nbx, 1, w.nsys, s));
   } else {
     // FP16/BF16 Krylov vectors: no t recurrence (its rounding would accumulate)
     a.fin = FIN_ALPHA;
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes, nbx * w.G, s, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes_k1, nbx * w.G, s, a));
     CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s));
   }
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
@@ -504,8 +577,9 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.fin = FIN_NORM;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes, nbx * w.G, s, a));
-  CK(launch_finalize(ctl, FIN_NORM, nbx, 2, w.nsys, s));
+  const int nbx2 = ds_blocks(c->Ve, w.lanes_k2);
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, nbx2 * w.G, s, a));
+  CK(launch_finalize(ctl, FIN_NORM, nbx2, 2, w.nsys, s));
   return STAG_OK;
 }
 
@@ -1210,14 +1284,14 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
   a.aux = w.r.arg();
   a.out = w.t.arg();
-  const int nb = ds_blocks(c->Ve, w.lanes) * w.G;
+  const int nb = ds_blocks(c->Ve, w.lanes_k1) * w.G;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes, nb, c->stream, a));
+  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes_k1, nb, c->stream, a));
   CK(cudaEventRecord(e0, c->stream));
   for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes, nb, c->stream, a));
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes_k1, nb, c->stream, a));
   CK(cudaEventRecord(e1, c->stream));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
