@@ -144,15 +144,26 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
                   int iters[], double true_res[]);
 
 /*
- * Average device time of one launch of the solver's first half-operator
- * kernel at `precision` -- t = D_oe (r + beta p), the direction update fused
- * into the neighbour gather, the dominant kernel of the CG iteration --
- * measured with CUDA events around `nlaunch` back-to-back launches on the
- * context stream, on the context's own internal vectors with the CG's launch
- * configuration.  `bytes_per_launch` (may be NULL) receives the kernel's
- * algorithmic bytes per launch: per output site 8 links, the two input
- * vectors r and p once, and the output vector once.
+ * Average device time of one launch of one of the two half-operator kernels
+ * of the CG iteration (Sec. 3, the even-odd operator of Eq. 2 split as
+ * A p = 4 m^2 p - D_eo (D_oe p)) at `precision`, measured with CUDA events
+ * on the context stream over `nlaunch` pairs of the two kernels launched
+ * alternately, as the iteration runs them (each starts on the cache state the
+ * other leaves), on the context's own internal vectors with the solver's
+ * launch configuration:
+ *   kernel 0: t = D_oe r + beta t_old (FP32/FP64 Krylov vectors) or
+ *             t = D_oe (r + beta p_old) (STAG_HALF_VECTORS), with |t|^2;
+ *   kernel 1: p = r + beta p_old, r -= alpha (4 m^2 p - D_eo t),
+ *             x += alpha p, with |r|^2 and Re<r, p>.
+ * `bytes_per_launch` (may be NULL) receives the kernel's algorithmic bytes
+ * per launch: per output site its 8 links and the gathered vector once, plus
+ * kernel 0: t_old (or r) read and t written; kernel 1: p, r and x read and
+ * written.  Returns STAG_ERR_ARG for another `kernel` or nlaunch < 1.
  */
+int stag_time_cg_kernel(stag_ctx *ctx, int precision, int kernel, int nlaunch, double *ms_per_launch,
+                        double *bytes_per_launch);
+
+/* stag_time_cg_kernel with kernel 0. */
 int stag_time_dslash(stag_ctx *ctx, int precision, int nlaunch, double *ms_per_launch,
                      double *bytes_per_launch);
 

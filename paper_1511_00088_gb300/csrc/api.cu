@@ -120,9 +120,11 @@ struct Work {
   int NS = 1, G = 1, NS64 = 1, G64 = 1;
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
   int lanes_k1 = 1, lanes_k2 = 1;  // lanes of the two CG kernels (tuned with their epilogues)
+  int nbx_k1 = 0, nbx_k2 = 0;      // blocks per system group of the two CG kernels
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
   DevBuf st, partials, tickets, flags;
+  DevBuf st2, partials2;  // second buffers of the states and partials (folded reductions)
   PinnedBuf h_st, h_flags;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -164,6 +166,9 @@ struct stag_ctx {
   std::string err;
   bool have_links = false;
   bool use_graph = true;
+  bool pdl = true;  // CG kernels launched as programmatic dependents of their predecessors
+  bool fold = true;     // each CG kernel finishes its predecessor's reduction itself
+  bool persist = true;  // CG kernels launched as one wave of resident blocks
   DevBuf links_canon;  // [4][V][3][3] FP64, kept for lazy reduced-precision copies
   DevBuf links64;
   DevBuf links_lo[4][2];
@@ -278,9 +283,10 @@ Ctl no_ctl() {
 // autotuner: lanes per output site of the half operator
 // ---------------------------------------------------------------------------
 // The choice (1 or 2 lanes per site) is made per (link precision, reconstruct,
-// vector precision, systems per thread, system groups, lattice) by timing both
-// candidates with CUDA events (3 warm-up and 10 timed launches of the plain
-// operator on the caller's buffers) and is cached for the process.  STAG_LANES
+// vector precision, systems per thread, system groups, lattice) by timing the
+// candidates with CUDA events (the plain operator: 3 warm-up and 10 timed
+// launches on the caller's buffers; the CG kernels: tune_cg_pair) and is
+// cached for the process.  STAG_LANES
 // = 1 or 2 forces a value; STAG_TUNE_CACHE names a text file that persists the
 // cache ("key lanes" lines) across processes.
 typedef std::tuple<int, int, int, int, int, int, int, int, int> TuneKey;
@@ -319,50 +325,88 @@ void tune_cache_store(const TuneKey &k, int lanes) {
 }
 
 // Time both mappings of one instantiation: `a` holds the kernel's arguments.
-int tune_lanes_epi(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, const DsArgs &a, int *lanes_out) {
+// Blocks per system group of a CG kernel with `lanes` lanes per site: one
+// wave of resident blocks over all groups (the kernel strides over its
+// chunks of sites), at most one block per chunk.
+int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes, int G, int *nbx) {
+  const int full = ds_blocks(c->Ve, lanes);
+  *nbx = full;
+  if (!c->persist) return STAG_OK;
+  DsArgs none;
+  memset(&none, 0, sizeof none);
+  const void *k = nullptr;
+  CK(launch_dslash(LP, recon, VP, VP, NS, EPI, lanes, 0, c->stream, none, &k));
+  int per_sm = 0, nsm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, DS_BT, 0));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  int n = per_sm * nsm / G;
+  if (n < 1) n = 1;
+  if (n < full) *nbx = n;
+  return STAG_OK;
+}
+
+// The lanes of the two CG kernels, chosen together: each of the four (lanes of
+// the first, lanes of the second) pairs runs 20 alternating launch pairs with
+// the solver's grids, twice in mirrored order, and the fastest total wins (the
+// iteration alternates the two kernels, each starting on the cache state the
+// other leaves).  Cached as 10 l1 + l2.
+int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, const DsArgs &a1, const DsArgs &a2,
+                 int *l1_out, int *l2_out) {
   const char *force = getenv("STAG_LANES");
   if (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) {
-    *lanes_out = force[0] - '0';
+    *l1_out = *l2_out = force[0] - '0';
     return STAG_OK;
   }
-  const int G = a.ngroups;
-  const TuneKey key(LP, recon, VP, NS * 16 + EPI, G, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+  const int G = a1.ngroups;
+  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, G, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *lanes_out = it->second;
+      *l1_out = it->second / 10;
+      *l2_out = it->second % 10;
       return STAG_OK;
     }
+  }
+  int nb1[3], nb2[3];
+  for (int l = 1; l <= 2; ++l) {
+    int n = 0;
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI1, l, G, &n));
+    nb1[l] = n * G;
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI_CG_K2, l, G, &n));
+    nb2[l] = n * G;
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_l = 1;
-  for (int l = 1; l <= 2; ++l) {
-    const int nb = ds_blocks(c->Ve, l) * G;
-    for (int i = 0; i < 3; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI, l, nb, c->stream, a));
-    CK(cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < 10; ++i) CK(launch_dslash(LP, recon, VP, VP, NS, EPI, l, nb, c->stream, a));
+  float tot[4] = {0.f, 0.f, 0.f, 0.f};
+  static const int order[8] = {0, 1, 2, 3, 3, 2, 1, 0};
+  for (int o = 0; o < 8; ++o) {
+    const int q = order[o], l1 = 1 + q / 2, l2 = 1 + q % 2;
+    for (int i = 0; i < 22; ++i) {
+      if (i == 2) CK(cudaEventRecord(e0, c->stream));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, l1, nb1[l1], c->stream, a1));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, l2, nb2[l2], c->stream, a2));
+    }
     CK(cudaEventRecord(e1, c->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_l = l;
-    }
+    tot[q] += ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  int best = 0;
+  for (int q = 1; q < 4; ++q)
+    if (tot[q] < tot[best]) best = q;
+  *l1_out = 1 + best / 2;
+  *l2_out = 1 + best % 2;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = best_l;
-    tune_cache_store(key, best_l);
+    g_tune[key] = 10 * *l1_out + *l2_out;
+    tune_cache_store(key, 10 * *l1_out + *l2_out);
   }
-  *lanes_out = best_l;
   return STAG_OK;
 }
 
@@ -462,6 +506,8 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.t.ensure(VP, nsys, Ve));
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
+  CK(w.st2.ensure(sizeof(SysState) * nsys));
+  CK(w.partials2.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
   const size_t ntickets = 1;
   CK(w.tickets.ensure(sizeof(unsigned) * ntickets));
   CK(w.flags.ensure(sizeof(int) * 4));
@@ -469,6 +515,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.h_flags.ensure(sizeof(int) * 4));
   CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * ntickets, c->stream));
   CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
+  CK(cudaMemsetAsync(w.st2.p, 0, sizeof(SysState) * nsys, c->stream));
   // defined contents for the timing entry point before any solve
   CK(cudaMemsetAsync(w.p.data.p, 0, w.p.data.n, c->stream));
   if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
@@ -491,14 +538,16 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a.aux = w.r.arg();
     a.xlo = w.x.arg();
     const bool rec = (VP == w.RP);
+    DsArgs a2 = a;
     a.par_out = 1;
     a.in = rec ? w.r.arg() : w.p.arg();
     a.out = w.t.arg();
-    CKS(tune_lanes_epi(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, &w.lanes_k1));
-    a.par_out = 0;
-    a.in = w.t.arg();
-    a.center = w.p.arg();
-    CKS(tune_lanes_epi(c, prec, recon, VP, w.NS, EPI_CG_K2, a, &w.lanes_k2));
+    a2.par_out = 0;
+    a2.in = w.t.arg();
+    a2.center = w.p.arg();
+    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, a2, &w.lanes_k1, &w.lanes_k2));
+    CKS(cg_blocks(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.G, &w.nbx_k1));
+    CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, &w.nbx_k2));
   }
   return STAG_OK;
 }
@@ -555,31 +604,98 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.gate = GATE_RUNNING;
   a.aux = w.r.arg();
   a.xlo = w.x.arg();
+  a.pdl = c->pdl ? 1 : 0;
   // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2) -> alpha
   a.par_out = 1;
   a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
   a.out = w.t.arg();
-  const int nbx = ds_blocks(c->Ve, w.lanes_k1);
+  const int nbx = w.nbx_k1;
   if (w.VP == w.RP) {
     // t = D_oe r + beta t_old: one gathered vector; |p|^2 from the scalar recurrence
     a.out = w.t.arg();
     a.fin = FIN_ALPHA_R;
     CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1R, w.lanes_k1, nbx * w.G, s, a));
-    CK(launch_finalize(ctl, FIN_ALPHA_R, nbx, 1, w.nsys, s));
+    CK(launch_finalize(ctl, FIN_ALPHA_R, nbx, 1, w.nsys, s, c->pdl));
   } else {
     // FP16/BF16 Krylov vectors: no t recurrence (its rounding would accumulate)
     a.fin = FIN_ALPHA;
     CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes_k1, nbx * w.G, s, a));
-    CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s));
+    CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s, c->pdl));
   }
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
   a.par_out = 0;
   a.in = w.t.arg();
   a.center = w.p.arg();
   a.fin = FIN_NORM;
-  const int nbx2 = ds_blocks(c->Ve, w.lanes_k2);
+  const int nbx2 = w.nbx_k2;
   CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, nbx2 * w.G, s, a));
-  CK(launch_finalize(ctl, FIN_NORM, nbx2, 2, w.nsys, s));
+  CK(launch_finalize(ctl, FIN_NORM, nbx2, 2, w.nsys, s, c->pdl));
+  return STAG_OK;
+}
+
+// One pass of the solve loop: SOLVE_UNROLL iterations.  With folded
+// reductions each CG kernel finishes its predecessor's reduction itself, so
+// the pass launches 2 SOLVE_UNROLL CG kernels and a single finalize kernel
+// (the last reduction, which also sets the loop and update conditions).  The
+// states and the partials alternate between two buffers, as a block may still
+// read the old ones while another writes the new; the pass starts and ends with
+// the states in w.st.
+int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
+  Work &w = c->w;
+  if (!c->fold) {
+    for (int u = 0; u < unroll; ++u) CKS(enqueue_main(c, s, ctl));
+    return STAG_OK;
+  }
+  const void *lo = nullptr;
+  CKS(links_for(c, w.prec, &lo));
+  SysState *S[2] = {(SysState *)w.st.p, (SysState *)w.st2.p};
+  double *PA = (double *)w.partials.p, *PB = (double *)w.partials2.p;
+  const bool rec = (w.VP == w.RP);
+  DsArgs a = ds_base(c);
+  a.links = lo;
+  a.nsys = w.nsys;
+  a.ngroups = w.G;
+  a.ctl = ctl;
+  a.gate = GATE_RUNNING;
+  a.fin = FIN_NONE;
+  a.aux = w.r.arg();
+  a.xlo = w.x.arg();
+  a.pdl = c->pdl ? 1 : 0;
+  int cur = 0;  // buffer of the current states
+  for (int u = 0; u < unroll; ++u) {
+    // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2); folds the previous K2's norms
+    a.par_out = 1;
+    a.in = rec ? w.r.arg() : w.p.arg();
+    a.out = w.t.arg();
+    a.center = VecArg();
+    a.ctl.st = S[cur];
+    a.ctl.partials = PA;
+    a.fold = (u == 0) ? FIN_NONE : FIN_NORM;
+    a.fold_partials = PB;
+    a.fold_nbx = w.nbx_k2;
+    a.fold_nv = 2;
+    a.st_out = S[1 - cur];
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.nbx_k1 * w.G,
+                     s, a));
+    if (u > 0) cur = 1 - cur;
+    // K2: p = r + beta p_old; r -= alpha (4 m^2 p - D_eo t); x += alpha p; folds K1's sums
+    a.par_out = 0;
+    a.in = w.t.arg();
+    a.out = VecArg();
+    a.center = w.p.arg();
+    a.ctl.st = S[cur];
+    a.ctl.partials = PB;
+    a.fold = rec ? FIN_ALPHA_R : FIN_ALPHA;
+    a.fold_partials = PA;
+    a.fold_nbx = w.nbx_k1;
+    a.fold_nv = rec ? 1 : 2;
+    a.st_out = S[1 - cur];
+    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, s, a));
+    cur = 1 - cur;
+  }
+  Ctl f = ctl;
+  f.partials = PB;
+  CK(launch_finalize(f, FIN_NORM, w.nbx_k2, 2, w.nsys, s, c->pdl, S[cur] == S[0] ? nullptr : S[cur]));
   return STAG_OK;
 }
 
@@ -675,7 +791,7 @@ int add_solve_loop(stag_ctx *c, cudaGraph_t g, const cudaGraphNode_t *deps, size
 
   CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int st = STAG_OK;
-  for (int u = 0; u < SOLVE_UNROLL && st == STAG_OK; ++u) st = enqueue_main(c, c->cap, ctl);
+  st = enqueue_pass(c, c->cap, ctl, SOLVE_UNROLL);
   if (st != STAG_OK) {
     cudaGraph_t tmp;
     cudaStreamEndCapture(c->cap, &tmp);
@@ -776,7 +892,7 @@ int solve_eager(stag_ctx *c, int maxiter) {
   for (long long it = 0; it <= (long long)maxiter + 2 * SOLVE_UNROLL * passes_per_poll;
        it += SOLVE_UNROLL * passes_per_poll) {
     for (int i = 0; i < passes_per_poll; ++i) {
-      for (int u = 0; u < SOLVE_UNROLL; ++u) CKS(enqueue_main(c, c->stream, ctl));
+      CKS(enqueue_pass(c, c->stream, ctl, SOLVE_UNROLL));
       CKS(enqueue_update(c, c->stream, ctl));
     }
     CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
@@ -1072,6 +1188,12 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   }
   const char *eager = getenv("STAG_EAGER");
   c->use_graph = !(eager && eager[0] == '1');
+  const char *pdl = getenv("STAG_PDL");
+  c->pdl = !(pdl && pdl[0] == '0');
+  const char *fold = getenv("STAG_FOLD");
+  c->fold = !(fold && fold[0] == '0');
+  const char *persist = getenv("STAG_PERSIST");
+  c->persist = !(persist && persist[0] == '0');
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1260,11 +1382,11 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
   return STAG_OK;
 }
 
-int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_launch,
-                     double *bytes_per_launch) {
+int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, double *ms_per_launch,
+                        double *bytes_per_launch) {
   if (!c) return STAG_ERR_ARG;
   int LP_, VP_, RP_;
-  if (!solver_precs(precision, &LP_, &VP_, &RP_) || nlaunch < 1 || !ms_per_launch)
+  if (!solver_precs(precision, &LP_, &VP_, &RP_) || nlaunch < 1 || !ms_per_launch || (kernel != 0 && kernel != 1))
     return arg_err(c, "bad argument");
   CK(cudaSetDevice(c->device));
   const int nsys = c->w.nsys > 0 && c->w.prec == LP_ && c->w.VP == VP_ ? c->w.nsys : 1;
@@ -1272,42 +1394,73 @@ int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_lau
   Work &w = c->w;
   const void *lo = nullptr;
   CKS(links_for(c, w.prec, &lo));
-  DsArgs a = ds_base(c);
-  a.links = lo;
-  a.nsys = w.nsys;
-  a.ngroups = w.G;
-  a.ctl = work_ctl(c, false);
-  a.gate = GATE_NONE;
-  a.fin = FIN_NONE;
-  a.par_out = 1;
-  const int k1 = (w.VP == w.RP) ? EPI_CG_K1R : EPI_CG_K1;
-  a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
-  a.aux = w.r.arg();
-  a.out = w.t.arg();
-  const int nb = ds_blocks(c->Ve, w.lanes_k1) * w.G;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes_k1, nb, c->stream, a));
-  CK(cudaEventRecord(e0, c->stream));
-  for (int i = 0; i < nlaunch; ++i)
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, k1, w.lanes_k1, nb, c->stream, a));
-  CK(cudaEventRecord(e1, c->stream));
-  CK(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *ms_per_launch = (double)ms / nlaunch;
+  // the two kernels with the solver's launch configuration (state zeroed:
+  // alpha = beta = 0, every system processed)
+  DsArgs a1 = ds_base(c);
+  a1.links = lo;
+  a1.nsys = w.nsys;
+  a1.ngroups = w.G;
+  a1.ctl = work_ctl(c, false);
+  a1.gate = GATE_NONE;
+  a1.fin = FIN_NONE;
+  a1.aux = w.r.arg();
+  a1.xlo = w.x.arg();
+  DsArgs a2 = a1;
+  a1.par_out = 1;
+  const int epi1 = (w.VP == w.RP) ? EPI_CG_K1R : EPI_CG_K1;
+  a1.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
+  a1.out = w.t.arg();
+  a2.par_out = 0;
+  a2.in = w.t.arg();
+  a2.center = w.p.arg();
+  // alternate them as the iteration does (so each starts with the cache the
+  // other leaves), an event between every two launches
+  std::vector<cudaEvent_t> ev(2 * (size_t)nlaunch + 1, nullptr);
+  int st = STAG_OK;
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) st = fail(c, STAG_ERR_CUDA, "cudaEventCreate", cudaGetLastError());
+  for (int i = 0; i < 2 && st == STAG_OK; ++i) {  // warm-up pair
+    if (launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi1, w.lanes_k1, w.nbx_k1 * w.G, c->stream, a1) != cudaSuccess ||
+        launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, c->stream, a2) != cudaSuccess)
+      st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
+  }
+  if (st == STAG_OK && cudaEventRecord(ev[0], c->stream) != cudaSuccess)
+    st = fail(c, STAG_ERR_CUDA, "cudaEventRecord", cudaGetLastError());
+  for (int i = 0; i < nlaunch && st == STAG_OK; ++i) {
+    if (launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi1, w.lanes_k1, w.nbx_k1 * w.G, c->stream, a1) != cudaSuccess ||
+        cudaEventRecord(ev[2 * i + 1], c->stream) != cudaSuccess ||
+        launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, c->stream, a2) != cudaSuccess ||
+        cudaEventRecord(ev[2 * i + 2], c->stream) != cudaSuccess)
+      st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
+  }
+  double tot = 0.0;
+  if (st == STAG_OK && cudaEventSynchronize(ev.back()) != cudaSuccess)
+    st = fail(c, STAG_ERR_CUDA, "cudaEventSynchronize", cudaGetLastError());
+  for (int i = 0; i < nlaunch && st == STAG_OK; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[2 * i + kernel], ev[2 * i + kernel + 1]) != cudaSuccess)
+      st = fail(c, STAG_ERR_CUDA, "cudaEventElapsedTime", cudaGetLastError());
+    tot += ms;
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st != STAG_OK) return st;
+  *ms_per_launch = tot / nlaunch;
   if (bytes_per_launch) {
     const double lb = (double)cplx_bytes(w.prec) * (w.recon ? 6 : 9);
     const double vb = (double)cplx_bytes(w.VP) * 3 + ((w.VP == P16 || w.VP == PBF) ? 4 : 0);
     const double rb = (double)cplx_bytes(w.RP) * 3;
-    // links once; gathered vectors once (through cache); t read (recurrence) or
-    // p_old read (gather form) and t written
-    *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * (2.0 * vb + rb));
+    // links once; the gathered vector once (through cache); then
+    //   first kernel: t_old read (recurrence) or p_old gathered (gather form), t written
+    //   second kernel: p read and written, r and x_lo read and written
+    const double per = (kernel == 0) ? (2.0 * vb + rb) : (3.0 * vb + 4.0 * rb);
+    *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * per);
   }
   return STAG_OK;
+}
+
+int stag_time_dslash(stag_ctx *c, int precision, int nlaunch, double *ms_per_launch, double *bytes_per_launch) {
+  return stag_time_cg_kernel(c, precision, 0, nlaunch, ms_per_launch, bytes_per_launch);
 }
 
 }  // extern "C"

@@ -5,12 +5,12 @@
 namespace stag {
 
 cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                          cudaStream_t st, const DsArgs &a) {
+                          cudaStream_t st, const DsArgs &a, const void **kptr) {
   switch (LP) {
-    case P64: return launch_dslash_p64(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
-    case P32: return launch_dslash_p32(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
-    case P16: return launch_dslash_p16(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
-    case PBF: return launch_dslash_pbf(recon, VP, OP, NS, EPI, lanes, nblocks, st, a);
+    case P64: return launch_dslash_p64(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
+    case P32: return launch_dslash_p32(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
+    case P16: return launch_dslash_p16(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
+    case PBF: return launch_dslash_pbf(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
   }
   return cudaErrorNotSupported;
 }
@@ -51,14 +51,17 @@ cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const B
 // used (partials, the system's state), the state is updated in registers and
 // stored once, and with a single system there is no cross-block ticket and no
 // fence (the next kernel in the stream sees the stores).
-__global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys) {
+__global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys,
+                                                     const SysState *st_in) {
   constexpr int PER = 4;  // partials per thread per value in flight at once
   __shared__ double red[NVMAX][FIN_BT / 32];
   __shared__ double sums[NVMAX];
   const int j = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  grid_dep_trigger();
+  grid_dep_wait();
   SysState st;
-  if (threadIdx.x == 0) st = c.st[j];
+  if (threadIdx.x == 0) st = (st_in != nullptr) ? st_in[j] : c.st[j];
   double acc[NVMAX];
 #pragma unroll
   for (int v = 0; v < NVMAX; ++v) acc[v] = 0.0;
@@ -91,10 +94,8 @@ __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int n
     if (fin == FIN_INIT) part = true;
     else if (fin == FIN_RESID) part = ((st.done == 0 || st.done == 3) && st.update != 0);
     else part = (st.done == 0);
-    if (part && fin != FIN_NONE) {
-      finalize_system(st, fin, sums);
-      c.st[j] = st;
-    }
+    if (part && fin != FIN_NONE) finalize_system(st, fin, sums);
+    if ((part && fin != FIN_NONE) || st_in != nullptr) c.st[j] = st;
   }
   int running = 0, upd = 0;
   if (nsys > 1) {
@@ -130,9 +131,9 @@ __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int n
 
 static inline int nblk(long long n, int bt) { return (int)((n + bt - 1) / bt); }
 
-cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st) {
-  k_finalize<<<nsys, FIN_BT, 0, st>>>(c, fin, nbx, nv, nsys);
-  return cudaGetLastError();
+cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st, bool pdl,
+                            const SysState *st_in) {
+  return launch_ex(k_finalize, nsys, FIN_BT, st, pdl, c, fin, nbx, nv, nsys, st_in);
 }
 
 cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st) {

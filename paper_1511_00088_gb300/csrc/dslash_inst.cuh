@@ -5,11 +5,16 @@
 
 #define STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_)                                      \
   if (recon == RC_ && VP == VP_ && OP == OP_ && NS == NS_ && EPI == EPI_) {              \
+    if (kptr != nullptr) {                                                               \
+      *kptr = (lanes == 2) ? (const void *)k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2> \
+                           : (const void *)k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1>; \
+      return cudaSuccess;                                                                \
+    }                                                                                    \
     if (lanes == 2)                                                                      \
-      k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2><<<nblocks, DS_BT, 0, st>>>(a);    \
-    else                                                                                 \
-      k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1><<<nblocks, DS_BT, 0, st>>>(a);    \
-    return cudaGetLastError();                                                           \
+      return launch_ex(k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2>, nblocks, DS_BT, st, \
+                       a.pdl != 0, a);                                                   \
+    return launch_ex(k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1>, nblocks, DS_BT, st,   \
+                     a.pdl != 0, a);                                                     \
   }
 
 // operator calls (plain, mass epilogue) and the two kernels of a CG iteration

@@ -2,7 +2,7 @@
 #include "dslash_inst.cuh"
 namespace stag {
 cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                              cudaStream_t st, const DsArgs &a) {
+                              cudaStream_t st, const DsArgs &a, const void **kptr) {
   STAG_DS_EPIS(P64, 0, P64, P64, 1)
   STAG_DS_EPIS(P64, 0, P64, P64, 4)
   STAG_DS_CASE(P64, 0, P64, P64, 1, EPI_RESID)

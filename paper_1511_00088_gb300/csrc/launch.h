@@ -15,24 +15,48 @@ inline int ds_blocks(int Ve, int lanes) {
 }
 constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
 
+// Launch kernel k on nblocks x bt threads in stream st.  With pdl the launch
+// carries programmatic stream serialisation: k may be scheduled while the
+// previous kernel in the stream drains, and must reach grid_dep_wait() before
+// it reads or writes anything that kernel touches.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*k)(KArgs...), int nblocks, int bt, cudaStream_t st, bool pdl,
+                             Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblocks);
+  cfg.blockDim = dim3((unsigned)bt);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args &&>(args)...);
+}
+
 // Launch k_dslash<LP, recon, VP, OP, NS, EPI, DS_BT, lanes> on `nblocks`
 // blocks (lanes = 1 or 2 lanes per output site).  Returns
 // cudaErrorNotSupported for a combination the library does not instantiate.
+// With kptr != nullptr nothing is launched: *kptr receives the kernel (for
+// occupancy queries).
 cudaError_t launch_dslash(int LP, int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                          cudaStream_t st, const DsArgs &a);
+                          cudaStream_t st, const DsArgs &a, const void **kptr = nullptr);
 cudaError_t launch_dslash_p64(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                              cudaStream_t st, const DsArgs &a);
+                              cudaStream_t st, const DsArgs &a, const void **kptr);
 cudaError_t launch_dslash_p32(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                              cudaStream_t st, const DsArgs &a);
+                              cudaStream_t st, const DsArgs &a, const void **kptr);
 cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                              cudaStream_t st, const DsArgs &a);
+                              cudaStream_t st, const DsArgs &a, const void **kptr);
 cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
-                              cudaStream_t st, const DsArgs &a);
+                              cudaStream_t st, const DsArgs &a, const void **kptr);
 
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 // k_finalize over the partials of the kernel just launched: nbx blocks per
-// system group, nv values per system
-cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st);
+// system group, nv values per system (pdl: launched as a programmatic
+// dependent of that kernel)
+cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cudaStream_t st,
+                            bool pdl = false, const SysState *st_in = nullptr);
 cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 
 cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st);

@@ -128,6 +128,16 @@ struct DsArgs {
   int nsys, ngroups;
   Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
   int gate, fin;
+  int pdl;               // launched as a programmatic dependent of the previous kernel
+  // Fold (fold != FIN_NONE): the reduction of the previous CG kernel, of kind
+  // `fold` (FIN_ALPHA, FIN_ALPHA_R or FIN_NORM) over fold_nv values and
+  // fold_nbx partials per system in fold_partials, is finished by every block
+  // of this kernel itself, from the states in ctl.st; the first block of each
+  // system group stores the new states to st_out.  fold_partials and st_out
+  // must not alias ctl.partials and ctl.st.
+  int fold, fold_nbx, fold_nv;
+  const double *fold_partials;
+  SysState *st_out;
 };
 
 struct BlasArgs {
@@ -363,6 +373,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may be scheduled while its predecessor in the stream is still
+// running; grid_dep_wait() returns once every predecessor grid has completed
+// and its writes are visible (a no-op for an ordinary launch), and nothing
+// before it touches memory.  grid_dep_trigger() lets the successor be
+// scheduled once every block of this grid has reached it.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// gate of one system by its state (GATE_RUNNING or GATE_UPDATE)
+__device__ __forceinline__ bool state_gate(const SysState &s, int gate) {
+  if (gate == GATE_RUNNING) return s.done == 0;
+  return (s.done == 0 || s.done == 3) && s.update != 0;
+}
+
 __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys) {
   if (j >= nsys) return false;
   if (gate == GATE_NONE || c.st == nullptr) return true;
@@ -456,6 +481,73 @@ __device__ __forceinline__ void finalize_system(SysState &s, int fin, const doub
   }
 }
 
+// The previous kernel's reduction, finished inside this kernel (DsArgs::fold):
+// every block sums the fold_nbx partials of each of its NS systems in the same
+// fixed order (a strided sum per thread, a warp tree, the warps in order) and
+// runs the same scalar logic on the same stored state, so all blocks hold
+// bit-identical states; the block with bx0 == 0 stores them.  The partials are
+// read straight after grid_dep_wait(), in one round of loads per thread.
+template <int NS, int BT>
+__device__ __forceinline__ void fold_state(const DsArgs &a, int j0, int bx0, SysState *sst) {
+  constexpr int NW = BT / 32;
+  constexpr int PER = (NS == 1) ? 8 : 1;  // partials per thread and value in flight at once
+  __shared__ double red[NS][NVMAX][NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nbx = a.fold_nbx, nv = a.fold_nv;
+  const long long ps = a.ctl.pstride;
+  double acc[NS][NVMAX];
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v) acc[k][v] = 0.0;
+  for (int base = 0; base < nbx; base += PER * BT) {
+    double x[NS][NVMAX][PER];
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+#pragma unroll
+      for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int i = base + u * BT + (int)threadIdx.x;
+          x[k][v][u] = (j0 + k < a.nsys && v < nv && i < nbx)
+                           ? a.fold_partials[((long long)(j0 + k) * NVMAX + v) * ps + i]
+                           : 0.0;
+        }
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+#pragma unroll
+      for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+        for (int u = 0; u < PER; ++u) acc[k][v] += x[k][v][u];
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v) {
+      const double w = warp_sum(acc[k][v]);
+      if (lane == 0) red[k][v][warp] = w;
+    }
+  __syncthreads();
+  if ((int)threadIdx.x < NS) {
+    const int k = threadIdx.x, j = j0 + k;
+    if (j < a.nsys) {
+      double sum[NVMAX];
+#pragma unroll
+      for (int v = 0; v < NVMAX; ++v) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += red[k][v][w];
+        sum[v] = t;
+      }
+      SysState st = a.ctl.st[j];
+      if (st.done == 0) finalize_system(st, a.fold, sum);
+      sst[k] = st;
+      if (bx0 == 0) a.st_out[j] = st;
+    }
+  }
+  __syncthreads();
+}
+
 // Reductions, in two stages (both with fixed summation order, so reruns are
 // bit-identical):
 //  1. block_partials, in every block of a reducing kernel: a 32-lane tree and
@@ -490,8 +582,10 @@ __device__ __forceinline__ void block_partials(const Ctl &c, T (&val)[NS][NV], i
 constexpr int FIN_BT = 1024;
 
 // grid = nsys blocks of FIN_BT threads; block j reduces system j's nv partial
-// arrays of nbx entries each (defined in blas.cu)
-__global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys);
+// arrays of nbx entries each (defined in blas.cu).  st_in != nullptr: the
+// states are read from st_in and all written to c.st (the other buffer of a
+// double-buffered pair); else updated in place in c.st.
+__global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys, const SysState *st_in);
 
 // ---------------------------------------------------------------------------
 // the half operator with fused epilogues
@@ -536,28 +630,48 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
   const Geom g = a.g;
   const int Ve = g.Ve;
   const int G = a.ngroups;
-  const int grp = blockIdx.x % G, bx = blockIdx.x / G;
+  const int grp = blockIdx.x % G, bx0 = blockIdx.x / G;
+  // The grid may hold fewer blocks than there are chunks of BT / LANES sites
+  // (one wave of resident blocks): each block then takes every nbx-th chunk
+  // and still leaves one partial per reduced value.
+  const int nbx = (int)gridDim.x / G;
+  constexpr int SPB = BT / LANES;  // sites per chunk
+  const int nchunk = (Ve + SPB - 1) / SPB;
   const int j0 = grp * NS;
   const int lane = LANES == 1 ? 0 : (int)(threadIdx.x % LANES);
-  const int s = bx * (BT / LANES) + (int)(threadIdx.x / LANES);
-  const bool valid = s < Ve;
+  grid_dep_trigger();
+  grid_dep_wait();
+  // the systems' states: as stored, or advanced past the previous kernel's
+  // reduction by this block (fold)
+  __shared__ SysState sst[NS];
+  const SysState *S = (a.ctl.st != nullptr) ? a.ctl.st + j0 : nullptr;
+  if (a.fold != FIN_NONE) {
+    fold_state<NS, BT>(a, j0, bx0, sst);
+    S = sst;
+  }
   bool act[NS];
-  R m4[NS], beta[NS];
+  R m4[NS], beta[NS], alpha[NS];
   bool any = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    act[k] = sys_gate(a.ctl, a.gate, j0 + k, a.nsys);
+    const bool in = j0 + k < a.nsys;
+    const bool has = S != nullptr && in;
+    act[k] = in && (a.gate == GATE_NONE || !has || state_gate(S[k], a.gate));
     any |= act[k];
-    const bool has = a.ctl.st != nullptr && j0 + k < a.nsys;
-    m4[k] = (R)(has ? a.ctl.st[j0 + k].m4 : a.m4_single);
-    beta[k] = (R)(has ? a.ctl.st[j0 + k].beta : 0.0);
+    m4[k] = (R)(has ? S[k].m4 : a.m4_single);
+    beta[k] = (R)(has ? S[k].beta : 0.0);
+    alpha[k] = (R)(has ? S[k].alpha : 0.0);
   }
   R part[NS][NV];  // per-thread reduction values (FP32 in the FP32-arithmetic kernels)
 #pragma unroll
   for (int k = 0; k < NS; ++k)
 #pragma unroll
     for (int v = 0; v < NV; ++v) part[k][v] = 0;
+  const int P = a.par_out;
 
+  for (int bx = bx0; bx < nchunk; bx += nbx) {
+  const int s = bx * SPB + (int)(threadIdx.x / LANES);
+  const bool valid = s < Ve;
   R acc[NS][6];
 #pragma unroll
   for (int k = 0; k < NS; ++k)
@@ -566,7 +680,6 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
 
   // centre vectors of the single-system epilogue, loaded up front (HOIST)
   R cpre[NC > 0 ? NC : 1][6];
-  const int P = a.par_out;
   if (any && valid) {
     if (HOIST && NC > 0) {
       if (EPI == EPI_CG_K2) {
@@ -705,7 +818,6 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
         // p_new; p_new, r, x_lo stored; |r|^2 and Re<r, p_new> reduced.  Ap itself
         // is never stored.
         R cv[6], rv[6], xv[6];
-        const R alpha = (R)a.ctl.st[j].alpha;
         if (valid) {
           if (HOIST) {
 #pragma unroll
@@ -723,8 +835,8 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
           for (int i = 0; i < 6; ++i) {
             cv[i] = rv[i] + beta[k] * cv[i];
             const R ap = m4[k] * cv[i] - acc[k][i];
-            rv[i] -= alpha * ap;
-            xv[i] += alpha * cv[i];
+            rv[i] -= alpha[k] * ap;
+            xv[i] += alpha[k] * cv[i];
           }
           R q = 0, rp = 0;
 #pragma unroll
@@ -819,9 +931,10 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
       store_site_share<OP, LANES>(a.out, j, s, Ve, lane, o);
     }
   }
+  }  // chunks
 
   if (EPI == EPI_CG_K1 || EPI == EPI_CG_K1R || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
-    if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx);
+    if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx0);
   }
 }
 

@@ -77,6 +77,7 @@ def load():
             "stag_mdagm": (I, [P, I, D, P, P]),
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
+            "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_force": (I, [P, P, P, P]),
@@ -170,6 +171,14 @@ def stag_time_dslash(ctx, precision, nlaunch):
     ms = ctypes.c_double(0.0)
     by = ctypes.c_double(0.0)
     st = load().stag_time_dslash(ctx, int(precision), int(nlaunch), ctypes.byref(ms), ctypes.byref(by))
+    return st, ms.value, by.value
+
+
+def stag_time_cg_kernel(ctx, precision, kernel, nlaunch):
+    ms = ctypes.c_double(0.0)
+    by = ctypes.c_double(0.0)
+    st = load().stag_time_cg_kernel(ctx, int(precision), int(kernel), int(nlaunch), ctypes.byref(ms),
+                                    ctypes.byref(by))
     return st, ms.value, by.value
 
 
@@ -348,5 +357,11 @@ class Context:
 
     def time_dslash(self, precision=STAG_FP32, nlaunch=50):
         st, ms, by = stag_time_dslash(self.h, precision, nlaunch)
+        self._check(st)
+        return ms, by
+
+    def time_cg_kernel(self, kernel, precision=STAG_FP32, nlaunch=50):
+        """(ms per launch, algorithmic bytes per launch) of CG kernel 0 or 1."""
+        st, ms, by = stag_time_cg_kernel(self.h, precision, kernel, nlaunch)
         self._check(st)
         return ms, by
