@@ -121,6 +121,8 @@ struct Work {
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
   int lanes_k1 = 1, lanes_k2 = 1;  // lanes of the two CG kernels (tuned with their epilogues)
   int nbx_k1 = 0, nbx_k2 = 0;      // blocks per system group of the two CG kernels
+  int tma = 0;                     // the CG kernels read bulk-copied tiled links
+  const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
   DevBuf st, partials, tickets, flags;
@@ -169,10 +171,13 @@ struct stag_ctx {
   bool pdl = true;  // CG kernels launched as programmatic dependents of their predecessors
   bool fold = true;     // each CG kernel finishes its predecessor's reduction itself
   bool persist = true;  // CG kernels launched as one wave of resident blocks
+  int tma_mode = 0;     // bulk-copied links in the single-system CG kernels: 0 off, 1 on, -1 tuned
   DevBuf links_canon;  // [4][V][3][3] FP64, kept for lazy reduced-precision copies
   DevBuf links64;
   DevBuf links_lo[4][2];
   bool lo_ok[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
+  DevBuf links_tile[4][2];  // tiled site-owned copies (bulk-copied by the CG kernels)
+  bool tile_ok[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
   DevBuf stage_in, stage_out;  // FP64 ABI-layout vectors for host transfers
   VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
   DevBuf defect;
@@ -271,6 +276,26 @@ int links_for(stag_ctx *c, int P, const void **out) {
   return STAG_OK;
 }
 
+// the tiled site-owned links at precision P (P32, P16 or PBF), built on first use
+int links_tile_for(stag_ctx *c, int P, const void **out) {
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  const int rc = (c->flags & STAG_RECON12) ? 1 : 0;
+  if (!c->tile_ok[P][rc]) {
+    const size_t ne = rc ? 6 : 9;
+    const size_t bytes = cplx_bytes(P) * ne * 8ull * LT * 2ull * (size_t)link_tiles(c->Ve);
+    CK(c->links_tile[P][rc].ensure(bytes));
+    CK(cudaMemsetAsync(c->links_tile[P][rc].p, 0, bytes, c->stream));
+    CK(launch_pack_links_tiled(P, rc, reinterpret_cast<const double2 *>(c->links_canon.p), c->links_tile[P][rc].p,
+                               c->g, link_tiles(c->Ve), c->stream));
+    c->tile_ok[P][rc] = true;
+  }
+  *out = c->links_tile[P][rc].p;
+  return STAG_OK;
+}
+
 int link_recon(const stag_ctx *c, int P) { return (P != P64 && (c->flags & STAG_RECON12)) ? 1 : 0; }
 
 Ctl no_ctl() {
@@ -328,16 +353,17 @@ void tune_cache_store(const TuneKey &k, int lanes) {
 // Blocks per system group of a CG kernel with `lanes` lanes per site: one
 // wave of resident blocks over all groups (the kernel strides over its
 // chunks of sites), at most one block per chunk.
-int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes, int G, int *nbx) {
+int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes, int G, int tma, int *nbx) {
   const int full = ds_blocks(c->Ve, lanes);
   *nbx = full;
   if (!c->persist) return STAG_OK;
   DsArgs none;
   memset(&none, 0, sizeof none);
+  none.tma = tma;
   const void *k = nullptr;
   CK(launch_dslash(LP, recon, VP, VP, NS, EPI, lanes, 0, c->stream, none, &k));
   int per_sm = 0, nsm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, DS_BT, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, DS_BT, tma ? tma_smem_bytes(LP, recon, lanes) : 0));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   int n = per_sm * nsm / G;
   if (n < 1) n = 1;
@@ -345,49 +371,68 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
   return STAG_OK;
 }
 
-// The lanes of the two CG kernels, chosen together: each of the four (lanes of
-// the first, lanes of the second) pairs runs 20 alternating launch pairs with
-// the solver's grids, twice in mirrored order, and the fastest total wins (the
-// iteration alternates the two kernels, each starting on the cache state the
-// other leaves).  Cached as 10 l1 + l2.
-int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, const DsArgs &a1, const DsArgs &a2,
-                 int *l1_out, int *l2_out) {
+// The launch form of the two CG kernels, chosen together: lanes per site of
+// each (1 or 2) and, where allowed (tma_ok: one system, reduced-precision
+// links), whether both read their links through bulk copies.  Each candidate
+// runs 20 alternating launch pairs with the solver's grids, twice (the second
+// sweep in reverse order), and the fastest total wins: the iteration
+// alternates the two kernels, each starting on the cache state the other
+// leaves.  Cached as 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2 fixes the
+// lanes; STAG_TMA = 1 turns the bulk-copied links on, = t lets the tuner
+// decide (default: off).
+int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArgs a1, DsArgs a2, bool tma_ok,
+                 int *l1_out, int *l2_out, int *tma_out) {
+  const int tma_lo = (tma_ok && c->tma_mode != 0) ? (c->tma_mode == 1 ? 1 : 0) : 0;
+  const int tma_hi = (tma_ok && c->tma_mode != 0) ? 1 : 0;
   const char *force = getenv("STAG_LANES");
-  if (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) {
-    *l1_out = *l2_out = force[0] - '0';
+  const int fl = (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) ? force[0] - '0' : 0;
+  if (fl && tma_lo == tma_hi) {
+    *l1_out = *l2_out = fl;
+    *tma_out = tma_lo;
     return STAG_OK;
   }
   const int G = a1.ngroups;
-  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, G, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
-  {
+  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, G * 4 + tma_lo * 2 + tma_hi, c->dims[0], c->dims[1],
+                    c->dims[2], c->dims[3]);
+  if (!fl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *l1_out = it->second / 10;
+      *tma_out = it->second / 100;
+      *l1_out = (it->second / 10) % 10;
       *l2_out = it->second % 10;
       return STAG_OK;
     }
   }
-  int nb1[3], nb2[3];
-  for (int l = 1; l <= 2; ++l) {
+  // candidates q = 4 tma + 2 (l1 - 1) + (l2 - 1)
+  std::vector<int> cand;
+  for (int t = tma_lo; t <= tma_hi; ++t)
+    for (int l1 = 1; l1 <= 2; ++l1)
+      for (int l2 = 1; l2 <= 2; ++l2)
+        if (!fl || (l1 == fl && l2 == fl)) cand.push_back(4 * t + 2 * (l1 - 1) + (l2 - 1));
+  int nb1[8], nb2[8];
+  for (int q : cand) {
+    const int t = q / 4, l1 = 1 + (q / 2) % 2, l2 = 1 + q % 2;
     int n = 0;
-    CKS(cg_blocks(c, LP, recon, VP, NS, EPI1, l, G, &n));
-    nb1[l] = n * G;
-    CKS(cg_blocks(c, LP, recon, VP, NS, EPI_CG_K2, l, G, &n));
-    nb2[l] = n * G;
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI1, l1, G, t, &n));
+    nb1[q] = n * G;
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI_CG_K2, l2, G, t, &n));
+    nb2[q] = n * G;
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float tot[4] = {0.f, 0.f, 0.f, 0.f};
-  static const int order[8] = {0, 1, 2, 3, 3, 2, 1, 0};
-  for (int o = 0; o < 8; ++o) {
-    const int q = order[o], l1 = 1 + q / 2, l2 = 1 + q % 2;
+  float tot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int nc = (int)cand.size();
+  for (int o = 0; o < 2 * nc; ++o) {
+    const int q = cand[o < nc ? o : 2 * nc - 1 - o];
+    const int t = q / 4, l1 = 1 + (q / 2) % 2, l2 = 1 + q % 2;
+    a1.tma = a2.tma = t;
     for (int i = 0; i < 22; ++i) {
       if (i == 2) CK(cudaEventRecord(e0, c->stream));
-      CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, l1, nb1[l1], c->stream, a1));
-      CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, l2, nb2[l2], c->stream, a2));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, l1, nb1[q], c->stream, a1));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, l2, nb2[q], c->stream, a2));
     }
     CK(cudaEventRecord(e1, c->stream));
     CK(cudaEventSynchronize(e1));
@@ -397,15 +442,17 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, const
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int best = 0;
-  for (int q = 1; q < 4; ++q)
+  int best = cand[0];
+  for (int q : cand)
     if (tot[q] < tot[best]) best = q;
-  *l1_out = 1 + best / 2;
+  *tma_out = best / 4;
+  *l1_out = 1 + (best / 2) % 2;
   *l2_out = 1 + best % 2;
-  {
+  if (!fl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = 10 * *l1_out + *l2_out;
-    tune_cache_store(key, 10 * *l1_out + *l2_out);
+    const int v = 100 * *tma_out + 10 * *l1_out + *l2_out;
+    g_tune[key] = v;
+    tune_cache_store(key, v);
   }
   return STAG_OK;
 }
@@ -510,9 +557,9 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   CK(w.partials2.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
   const size_t ntickets = 1;
   CK(w.tickets.ensure(sizeof(unsigned) * ntickets));
-  CK(w.flags.ensure(sizeof(int) * 4));
+  CK(w.flags.ensure(sizeof(int) * 8));
   CK(w.h_st.ensure(sizeof(SysState) * nsys));
-  CK(w.h_flags.ensure(sizeof(int) * 4));
+  CK(w.h_flags.ensure(sizeof(int) * 8));
   CK(cudaMemsetAsync(w.tickets.p, 0, sizeof(unsigned) * ntickets, c->stream));
   CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
   CK(cudaMemsetAsync(w.st2.p, 0, sizeof(SysState) * nsys, c->stream));
@@ -537,6 +584,11 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a.fin = FIN_NONE;
     a.aux = w.r.arg();
     a.xlo = w.x.arg();
+    const bool tma_ok = (w.NS == 1 && prec != P64 && c->tma_mode != 0);
+    w.links_tile = nullptr;
+    if (tma_ok) CKS(links_tile_for(c, prec, &w.links_tile));
+    a.links_tile = w.links_tile;
+    a.ntile = link_tiles(c->Ve);
     const bool rec = (VP == w.RP);
     DsArgs a2 = a;
     a.par_out = 1;
@@ -545,9 +597,10 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a2.par_out = 0;
     a2.in = w.t.arg();
     a2.center = w.p.arg();
-    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, a2, &w.lanes_k1, &w.lanes_k2));
-    CKS(cg_blocks(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.G, &w.nbx_k1));
-    CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, &w.nbx_k2));
+    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, a2, tma_ok, &w.lanes_k1,
+                     &w.lanes_k2, &w.tma));
+    CKS(cg_blocks(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
+    CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, w.tma, &w.nbx_k2));
   }
   return STAG_OK;
 }
@@ -605,6 +658,10 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.aux = w.r.arg();
   a.xlo = w.x.arg();
   a.pdl = c->pdl ? 1 : 0;
+  if (w.tma) CKS(links_tile_for(c, w.prec, &w.links_tile));
+  a.tma = w.tma;
+  a.links_tile = w.links_tile;
+  a.ntile = link_tiles(c->Ve);
   // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2) -> alpha
   a.par_out = 1;
   a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
@@ -661,6 +718,10 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
   a.aux = w.r.arg();
   a.xlo = w.x.arg();
   a.pdl = c->pdl ? 1 : 0;
+  if (w.tma) CKS(links_tile_for(c, w.prec, &w.links_tile));
+  a.tma = w.tma;
+  a.links_tile = w.links_tile;
+  a.ntile = link_tiles(c->Ve);
   int cur = 0;  // buffer of the current states
   for (int u = 0; u < unroll; ++u) {
     // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2); folds the previous K2's norms
@@ -870,7 +931,8 @@ int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double m
     hf[1] = 0;
     hf[2] = 0;
     hf[3] = maxiter + 8;
-    CK(cudaMemcpyAsync(w.flags.p, hf, sizeof(int) * 4, cudaMemcpyHostToDevice, c->stream));
+    for (int i = 4; i < 8; ++i) hf[i] = 0;  // [4]: a bulk-copy wait in a CG kernel gave up
+    CK(cudaMemcpyAsync(w.flags.p, hf, sizeof(int) * 8, cudaMemcpyHostToDevice, c->stream));
   }
   {
     const Ctl ctl0 = work_ctl(c, false);
@@ -907,10 +969,16 @@ int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[])
   Work &w = c->w;
   const int nsys = w.nsys;
   SysState *hs = (SysState *)w.h_st.p;
+  int *hf = (int *)w.h_flags.p;
   CK(cudaMemcpyAsync(hs, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
   for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
   CK(cudaStreamSynchronize(c->stream));
   c->last_nsys = nsys;
+  if (hf[4] != 0) {
+    c->err = "a CG kernel gave up waiting for its bulk-copied links; the solution is void";
+    return STAG_ERR_CUDA;
+  }
   int status = STAG_OK;
   for (int j = 0; j < nsys; ++j) {
     if (iters) iters[j] = hs[j].iter;
@@ -1194,6 +1262,10 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   c->fold = !(fold && fold[0] == '0');
   const char *persist = getenv("STAG_PERSIST");
   c->persist = !(persist && persist[0] == '0');
+  const char *tma = getenv("STAG_TMA");
+  // measured slower than the register path at FP32 and FP16 (shared memory
+  // caps the sites in flight per SM below what the registers hold), so opt-in
+  c->tma_mode = (tma && tma[0] == '1') ? 1 : (tma && tma[0] == 't') ? -1 : 0;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1244,7 +1316,7 @@ int stag_links_upload(stag_ctx *c, const double *links) {
   CK(c->links64.ensure(cplx_bytes(P64) * 9ull * 8ull * c->Ve));
   CK(launch_pack_links(P64, 0, reinterpret_cast<const double2 *>(c->links_canon.p), c->links64.p, c->g,
                        c->stream));
-  for (int p = 0; p < 4; ++p) c->lo_ok[p][0] = c->lo_ok[p][1] = false;
+  for (int p = 0; p < 4; ++p) c->lo_ok[p][0] = c->lo_ok[p][1] = c->tile_ok[p][0] = c->tile_ok[p][1] = false;
   c->have_links = true;
   c->w.drop_graph();  // the graph holds link pointers of the reduced-precision copies
   CK(cudaStreamSynchronize(c->stream));
@@ -1405,6 +1477,10 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   a1.fin = FIN_NONE;
   a1.aux = w.r.arg();
   a1.xlo = w.x.arg();
+  if (w.tma) CKS(links_tile_for(c, w.prec, &w.links_tile));
+  a1.tma = w.tma;
+  a1.links_tile = w.links_tile;
+  a1.ntile = link_tiles(c->Ve);
   DsArgs a2 = a1;
   a1.par_out = 1;
   const int epi1 = (w.VP == w.RP) ? EPI_CG_K1R : EPI_CG_K1;

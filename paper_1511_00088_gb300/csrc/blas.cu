@@ -174,6 +174,19 @@ cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int ns
   return cudaErrorNotSupported;
 }
 
+cudaError_t launch_pack_links_tiled(int LP, int recon, const double2 *src, void *dst, Geom g, int ntile,
+                                    cudaStream_t st) {
+  const int nb = nblk(16ll * g.Ve, 256);
+#define STAG_PLT(P_, R_)                                                        \
+  if (LP == P_ && recon == R_) {                                                \
+    k_pack_links_tiled<P_, R_><<<nb, 256, 0, st>>>(src, dst, g, ntile);         \
+    return cudaGetLastError();                                                  \
+  }
+  STAG_PLT(P32, 0) STAG_PLT(P32, 1) STAG_PLT(P16, 0) STAG_PLT(P16, 1) STAG_PLT(PBF, 0) STAG_PLT(PBF, 1)
+#undef STAG_PLT
+  return cudaErrorNotSupported;
+}
+
 cudaError_t launch_pack_links(int LP, int recon, const double2 *src, void *dst, Geom g,
                               cudaStream_t st) {
   const long long n = 8ll * g.Ve;  // 4 V links

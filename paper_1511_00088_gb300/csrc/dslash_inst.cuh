@@ -3,18 +3,43 @@
 #pragma once
 #include "launch.h"
 
+namespace stag {
+// one instantiation of the half operator: launch it, or (kptr) return it; with
+// a.tma the bulk-copied-links variant where it exists
+template <int LP_, int RC_, int VP_, int OP_, int NS_, int EPI_, int L_>
+cudaError_t ds_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **kptr) {
+  constexpr bool CAN_TMA =
+      NS_ == 1 && LP_ != P64 && (EPI_ == EPI_CG_K1 || EPI_ == EPI_CG_K1R || EPI_ == EPI_CG_K2);
+  if constexpr (CAN_TMA) {
+    if (a.tma) {
+      auto k = k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, L_, 1>;
+      const unsigned smem = tma_smem_bytes(LP_, RC_, L_);
+      static bool attr_set = false;  // benign race: setting it twice is harmless
+      if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+      }
+      if (kptr) {
+        *kptr = (const void *)k;
+        return cudaSuccess;
+      }
+      return launch_ex_smem(k, nblocks, DS_BT, smem, st, a.pdl != 0, a);
+    }
+  }
+  auto k = k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, L_>;
+  if (kptr) {
+    *kptr = (const void *)k;
+    return cudaSuccess;
+  }
+  return launch_ex(k, nblocks, DS_BT, st, a.pdl != 0, a);
+}
+}  // namespace stag
+
 #define STAG_DS_CASE(LP_, RC_, VP_, OP_, NS_, EPI_)                                      \
   if (recon == RC_ && VP == VP_ && OP == OP_ && NS == NS_ && EPI == EPI_) {              \
-    if (kptr != nullptr) {                                                               \
-      *kptr = (lanes == 2) ? (const void *)k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2> \
-                           : (const void *)k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1>; \
-      return cudaSuccess;                                                                \
-    }                                                                                    \
-    if (lanes == 2)                                                                      \
-      return launch_ex(k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 2>, nblocks, DS_BT, st, \
-                       a.pdl != 0, a);                                                   \
-    return launch_ex(k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, 1>, nblocks, DS_BT, st,   \
-                     a.pdl != 0, a);                                                     \
+    if (lanes == 2) return ds_one<LP_, RC_, VP_, OP_, NS_, EPI_, 2>(nblocks, st, a, kptr); \
+    return ds_one<LP_, RC_, VP_, OP_, NS_, EPI_, 1>(nblocks, st, a, kptr);              \
   }
 
 // operator calls (plain, mass epilogue) and the two kernels of a CG iteration

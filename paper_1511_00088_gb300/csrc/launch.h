@@ -20,12 +20,12 @@ constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
 // previous kernel in the stream drains, and must reach grid_dep_wait() before
 // it reads or writes anything that kernel touches.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_ex(void (*k)(KArgs...), int nblocks, int bt, cudaStream_t st, bool pdl,
-                             Args &&...args) {
+inline cudaError_t launch_ex_smem(void (*k)(KArgs...), int nblocks, int bt, unsigned smem, cudaStream_t st,
+                                  bool pdl, Args &&...args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblocks);
   cfg.blockDim = dim3((unsigned)bt);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -34,6 +34,20 @@ inline cudaError_t launch_ex(void (*k)(KArgs...), int nblocks, int bt, cudaStrea
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, static_cast<Args &&>(args)...);
 }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*k)(KArgs...), int nblocks, int bt, cudaStream_t st, bool pdl,
+                             Args &&...args) {
+  return launch_ex_smem(k, nblocks, bt, 0u, st, pdl, static_cast<Args &&>(args)...);
+}
+
+// dynamic shared memory of a half-operator kernel with bulk-copied links
+// (DsArgs::tma): TMA_STAGES chunks of DS_BT / lanes sites x 8 links
+inline unsigned tma_smem_bytes(int LP, int recon, int lanes) {
+  const unsigned cb = (LP == P32) ? 8u : 4u;
+  return (unsigned)TMA_STAGES * (unsigned)(DS_BT / lanes) * 8u * (recon ? 6u : 9u) * cb;
+}
+// tiles per parity of the tiled site-owned links (whole chunks of DS_BT sites)
+inline int link_tiles(int Ve) { return (Ve + DS_BT - 1) / DS_BT * (DS_BT / LT); }
 
 // Launch k_dslash<LP, recon, VP, OP, NS, EPI, DS_BT, lanes> on `nblocks`
 // blocks (lanes = 1 or 2 lanes per output site).  Returns
@@ -65,6 +79,9 @@ cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int ns
                                cudaStream_t st);
 cudaError_t launch_pack_links(int LP, int recon, const double2 *src, void *dst, Geom g,
                               cudaStream_t st);
+// the tiled site-owned copy (LP = P32, P16 or PBF); dst already zeroed
+cudaError_t launch_pack_links_tiled(int LP, int recon, const double2 *src, void *dst, Geom g, int ntile,
+                                    cudaStream_t st);
 cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
                               cudaStream_t st);
 

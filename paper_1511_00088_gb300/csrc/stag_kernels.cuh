@@ -14,6 +14,11 @@
 //          reconstruct-12 where row 2 = conj(row0 x row1) is rebuilt in registers)
 //   vector [system][colour][Ve] complex; FP16/BF16 vectors add one FP32 scale
 //          per site and system: value = code * scale, scale = max |component|.
+//   tiled site-owned links (the single-system CG kernels at FP32/FP16/BF16):
+//          [parity][tile of LT sites][slot l][element e][LT] complex, slot
+//          mu = U_mu(x), slot 4 + mu = U_mu(x - mu) (the backward link, stored
+//          again at the site that uses it), so the 8 links of a chunk of sites
+//          are one contiguous block, moved into shared memory by one bulk copy.
 // One thread owns one output site and NS systems; the 8 links of the site are
 // loaded once into registers and applied to all NS systems.
 #pragma once
@@ -138,6 +143,10 @@ struct DsArgs {
   int fold, fold_nbx, fold_nv;
   const double *fold_partials;
   SysState *st_out;
+  // tma != 0 (single-system CG kernels): the links are read from links_tile
+  // (the tiled site-owned copy, ntile tiles per parity) through shared memory
+  int tma, ntile;
+  const void *links_tile;
 };
 
 struct BlasArgs {
@@ -281,14 +290,17 @@ __device__ __forceinline__ void store_site_share(const VecArg &f, int k, int s, 
 // ---------------------------------------------------------------------------
 // links
 // ---------------------------------------------------------------------------
-template <int LP, int RECON, class R>
-__device__ __forceinline__ void load_link(const void *base, int Ve, int par, int mu, int s, R (&u)[18]) {
-  typedef typename Tr<LP>::S2 S2;
+constexpr int LT = 64;  // sites per tile of the tiled site-owned link layout
+constexpr int TMA_STAGES = 2;  // shared-memory stages of the bulk-copied links
+
+// one link from its NE element planes at p, p + stride, ... (SMEM: shared
+// memory, else global through the read-only path); row 2 rebuilt for RECON
+template <int LP, int RECON, bool SMEM, class R>
+__device__ __forceinline__ void load_link_at(const typename Tr<LP>::S2 *p, long long stride, R (&u)[18]) {
   constexpr int NE = RECON ? 6 : 9;
-  const S2 *p = reinterpret_cast<const S2 *>(base) + (long long)((par * 4 + mu) * NE) * Ve + s;
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
-    auto w = to_r2(ldg2(p + (long long)e * Ve));
+    auto w = to_r2(SMEM ? p[e * stride] : ldg2(p + e * stride));
     u[2 * e] = (R)w.x;
     u[2 * e + 1] = (R)w.y;
   }
@@ -306,6 +318,51 @@ __device__ __forceinline__ void load_link(const void *base, int Ve, int par, int
       u[12 + 2 * c + 1] = -im;
     }
   }
+}
+
+template <int LP, int RECON, class R>
+__device__ __forceinline__ void load_link(const void *base, int Ve, int par, int mu, int s, R (&u)[18]) {
+  typedef typename Tr<LP>::S2 S2;
+  constexpr int NE = RECON ? 6 : 9;
+  load_link_at<LP, RECON, false>(reinterpret_cast<const S2 *>(base) + (long long)((par * 4 + mu) * NE) * Ve + s,
+                                 (long long)Ve, u);
+}
+
+// ---------------------------------------------------------------------------
+// bulk copies into shared memory (the TMA engine), completed on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier shared-memory accesses (and, after a block
+// barrier, the block's) before its later bulk copies into shared memory
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bytes (a multiple of 16; both addresses 16-byte aligned) from global src to
+// shared dst; the barrier's current phase completes when they have landed
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// wait until the phase with parity `parity` of the barrier has completed;
+// gives up (false) after 2^20 polls, each of which the hardware may suspend
+// for a bounded time
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  const uint32_t b = smem_addr(bar);
+  for (int i = 0; i < (1 << 20); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 // acc += sgn * (U v)
@@ -613,9 +670,16 @@ __global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys, cons
 // thread's directions are all in flight together (measured: 27 us instead of
 // 34 us for D_oe at 20^3 x 64, FP32).
 // (The FP64 kernels are bound by GB300's FP64 pipe and keep 4 blocks per SM.)
-template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES>
+// TMA (one system, FP32/FP16/BF16 links): the links come from the tiled
+// site-owned copy through a two-stage ring in dynamic shared memory; one
+// thread issues each chunk's bulk copy a round ahead (the first before the
+// wait for the predecessor grid, as the links never change during a solve),
+// so the link stream needs no registers and overlaps the arithmetic.
+template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES, int TMA = 0>
 __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a) {
+  static_assert(!TMA || (NS == 1 && LP != P64), "bulk-copied links: one system, reduced-precision links");
   typedef typename Tr<LP>::R R;
+  typedef typename Tr<LP>::S2 LS2;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
   constexpr bool XPAY_GATHER = (EPI == EPI_CG_K1);  // fold r + beta p into the neighbour gather
   // reduction values per system: K1 |t|^2, |p|^2; K2 |r|^2, Re<r,p>; RESID
@@ -640,6 +704,27 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
   const int j0 = grp * NS;
   const int lane = LANES == 1 ? 0 : (int)(threadIdx.x % LANES);
   grid_dep_trigger();
+  // bulk-copied links: NSTG stages of CHUNK bytes (this block's chunks in turn)
+  constexpr int NSTG = TMA_STAGES;
+  constexpr int NEL = RECON ? 6 : 9;
+  constexpr unsigned CHUNK = (unsigned)(SPB * 8 * NEL * sizeof(LS2));
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  __shared__ __align__(8) uint64_t stage_bar[NSTG];
+  const int nmine = bx0 < nchunk ? (nchunk - 1 - bx0) / nbx + 1 : 0;  // chunks of this block
+  auto issue = [&](int q) {  // bulk copy of this block's chunk q into stage q % NSTG
+    const LS2 *src = reinterpret_cast<const LS2 *>(a.links_tile) +
+                     ((long long)a.par_out * a.ntile + (long long)(bx0 + q * nbx) * (SPB / LT)) * (8 * NEL * LT);
+    bulk_copy_g2s(stage_mem + (q % NSTG) * CHUNK, src, CHUNK, &stage_bar[q % NSTG]);
+  };
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < NSTG; ++q) mbar_init(&stage_bar[q], 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int q = 0; q < NSTG - 1 && q < nmine; ++q) issue(q);
+  }
   grid_dep_wait();
   // the systems' states: as stored, or advanced past the previous kernel's
   // reduction by this block (fold)
@@ -669,7 +754,19 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
     for (int v = 0; v < NV; ++v) part[k][v] = 0;
   const int P = a.par_out;
 
-  for (int bx = bx0; bx < nchunk; bx += nbx) {
+  int round = 0;
+  for (int bx = bx0; bx < nchunk; bx += nbx, ++round) {
+  const LS2 *lsm = nullptr;  // this round's links in shared memory (TMA)
+  if (TMA) {
+    if (round > 0) __syncthreads();  // every thread is done with the stage read last round
+    if (threadIdx.x == 0 && round + NSTG - 1 < nmine) {
+      fence_proxy_async_smem();
+      issue(round + NSTG - 1);
+    }
+    if (!mbar_wait(&stage_bar[round % NSTG], (unsigned)(round / NSTG) & 1u) && a.ctl.flags != nullptr)
+      atomicExch(a.ctl.flags + 4, 1);  // reported by the host; the round's results are void
+    lsm = reinterpret_cast<const LS2 *>(stage_mem + (round % NSTG) * CHUNK);
+  }
   const int s = bx * SPB + (int)(threadIdx.x / LANES);
   const bool valid = s < Ve;
   R acc[NS][6];
@@ -729,8 +826,15 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
 #pragma unroll
       for (int dd = 0; dd < DPL; ++dd) {
         const int mu = lane * DPL + dd;
-        load_link<LP, RECON>(a.links, Ve, P, mu, s, uf[dd]);
-        load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb[dd], ub[dd]);
+        if (TMA) {
+          const int i = (int)threadIdx.x / LANES;  // site within the chunk
+          const LS2 *q = lsm + (i / LT) * (8 * NEL * LT) + i % LT;
+          load_link_at<LP, RECON, true>(q + mu * (NEL * LT), LT, uf[dd]);
+          load_link_at<LP, RECON, true>(q + (4 + mu) * (NEL * LT), LT, ub[dd]);
+        } else {
+          load_link<LP, RECON>(a.links, Ve, P, mu, s, uf[dd]);
+          load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb[dd], ub[dd]);
+        }
         load_vec<VP>(a.in, j0, sf[dd], Ve, vf[dd]);
         load_vec<VP>(a.in, j0, sb[dd], Ve, vb[dd]);
       }
@@ -1086,6 +1190,37 @@ __global__ void k_pack_links(const double2 *__restrict__ src, void *dst, Geom g)
       im = (R)__double2float_rn(w.y);
     }
     d[(long long)e * g.Ve] = from_r<LP>(re, im);
+  }
+}
+
+// tiled site-owned copy of the links (see the layout notes at the top): one
+// thread per (parity, site, slot); dst zeroed beforehand (the tail of the last
+// tiles stays zero); ntile tiles per parity
+template <int LP, int RECON>
+__global__ void k_pack_links_tiled(const double2 *__restrict__ src, void *dst, Geom g, int ntile) {
+  typedef typename Tr<LP>::S2 S2;
+  typedef typename Tr<LP>::R R;
+  constexpr int NE = RECON ? 6 : 9;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over 2 Ve 8
+  if (i >= 16ll * g.Ve) return;
+  const int l = (int)(i & 7);
+  const long long ps = i >> 3;
+  const int par = (int)(ps / g.Ve), s = (int)(ps % g.Ve);
+  int x[4];
+  site_coords(g, par, s, x);
+  const int mu = l & 3;
+  if (l >= 4) {  // the backward link U_mu(x - mu) lives at the neighbour
+    const int Lmu = mu == 0 ? g.L0 : mu == 1 ? g.L1 : mu == 2 ? g.L2 : g.L3;
+    x[mu] = (x[mu] == 0) ? Lmu - 1 : x[mu] - 1;
+  }
+  const long long lex = x[0] + (long long)g.L0 * (x[1] + (long long)g.L1 * (x[2] + (long long)g.L2 * x[3]));
+  const double2 *w = src + ((long long)mu * 2 * g.Ve + lex) * 9;
+  S2 *d = reinterpret_cast<S2 *>(dst) + (((long long)par * ntile + s / LT) * 8 + l) * NE * LT + s % LT;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    // FP64 -> FP32 first; FP16/BF16 round that FP32 value (as k_pack_links)
+    const R re = (R)__double2float_rn(w[e].x), im = (R)__double2float_rn(w[e].y);
+    d[(long long)e * LT] = from_r<LP>(re, im);
   }
 }
 
