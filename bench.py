@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--links", default="recon12", choices=["full", "recon12"],
                     help="storage of the reduced-precision links (the FP64 copy is always full)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="sources solved together in one call (the 48^3x96 workload uses 16)")
+    ap.add_argument("--seed-config", type=int, default=1,
+                    help="config number of the input seeds (1000 * config + stream)")
     ap.add_argument("--no-extras", action="store_true",
                     help="profiling runs: skip the comparison solves, the e2e leg and the CPU baseline")
     return ap.parse_args()
@@ -76,12 +80,12 @@ def link_mb(L, prec, links):
     return 4 * math.prod(L) * (6 if links == "recon12" else 9) * cb / 1e6
 
 
-def workload_config(L, mass, tol, prec, links="full"):
+def workload_config(L, mass, tol, prec, links="full", nrhs=1):
     return {
         "link_storage": ("reconstruct-12 (rows 0, 1 stored; row 2 = conj(row0 x row1) in registers)"
                          if links == "recon12" else "full 3x3") + f" at {prec.upper()}; FP64 copy full",
         "workload": f"{L[0]}^3x{L[3]} even-odd staggered CG, {prec.upper()} inner iteration, "
-                    f"FP64 reliable updates (delta=0.1), m={mass}, 1 RHS, true residual {tol:g}"
+                    f"FP64 reliable updates (delta=0.1), m={mass}, {nrhs} RHS, true residual {tol:g}"
         if L[0] == L[1] == L[2] else f"{L} staggered CG",
         "lattice": list(L),
         "links": "reunitarised exp(0.4 i H), synthetic (stands in for the MILC 20^3x64 ensemble)",
@@ -249,19 +253,28 @@ def run_ours(args):
     L = tuple(int(v) for v in args.lattice.split(","))
     V = synth.volume(L)
     Ve = V // 2
-    U = synth.random_links(L, 0.4, synth.seed_for(1, 1))
-    b = synth.gaussian_vector(Ve, synth.seed_for(1, 2 + rank))
+    cfg = args.seed_config
+    if V > (1 << 22):  # the numpy eigendecomposition is slow at this size: same recipe on the GPU
+        Ud = synth.random_links_device(L, 0.4, synth.seed_for(cfg, 1), device="cuda")
+        U = None
+    else:
+        U = synth.random_links(L, 0.4, synth.seed_for(cfg, 1))
+        Ud = torch.from_numpy(U).cuda()
+    nrhs = args.nrhs
+    bs = [synth.gaussian_vector(Ve, synth.seed_for(cfg, 2 + rank * nrhs + r)) for r in range(nrhs)]
+    b = bs[0]
     stream = torch.cuda.current_stream()
     ctx = stag.Context(L, recon12=(args.links == "recon12"), stream=stream.cuda_stream)
-    ctx.links_upload(torch.from_numpy(U).cuda())
-    bd = torch.from_numpy(b).cuda()
-    xd = torch.empty_like(bd)
+    ctx.links_upload(Ud)
+    bds = [torch.from_numpy(v).cuda() for v in bs]
+    xds = [torch.empty_like(v) for v in bds]
+    bd, xd = bds[0], xds[0]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def solve():
-        xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=50000,
-                                      precision=prec, xs=[xd])
-        return int(it[0]), float(tr[0])
+        xs, st, it, tr = ctx.cg_solve(bds, [args.mass], tol=args.tol, maxiter=50000,
+                                      precision=prec, xs=xds)
+        return [int(v) for v in it], float(max(tr))
 
     for _ in range(args.warmup):
         solve()
@@ -284,19 +297,20 @@ def run_ours(args):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         _, nu, _ = ctx.solve_stats(0)
+        passes, ups = ctx.solve_counters()
         iters.append(it)
         updates.append(nu)
         res.append(tr)
-        # pack, init + its finalize, unpack; per pass of 4 iterations 8 CG
-        # kernels and one finalize; per reliable update 5 kernels
-        launches += 4 + 9 * (-(-it // 4)) + 5 * nu
+        # one pack per source, init + its finalize, one unpack per system; per
+        # loop pass 8 CG kernels and one finalize; per update step 5 kernels
+        launches += 2 * nrhs + 2 + 9 * passes + 5 * ups
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_step = total_ms / args.steps
-    flops_step = FLOP_PER_SITE_ITER * Ve * statistics.mean(iters)
+    flops_step = FLOP_PER_SITE_ITER * Ve * statistics.mean(sum(i) for i in iters)
     if dist:
         t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -309,17 +323,17 @@ def run_ours(args):
     value = flops_all / (ms_step * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers (pinned), copies inside
-    bh = torch.from_numpy(b).pin_memory()
-    xh = torch.empty_like(bh).pin_memory()
+    bhs = [torch.from_numpy(v).pin_memory() for v in bs]
+    xhs = [torch.empty_like(v).pin_memory() for v in bhs]
     e2e_ms, e2e_it = [], []
     for k in range(0 if args.no_extras else max(1, min(args.steps, 5))):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t = time.perf_counter()
-        xs, st, it, tr = ctx.cg_solve([bh], [args.mass], tol=args.tol, maxiter=50000,
-                                      precision=prec, xs=[xh])
+        xs, st, it, tr = ctx.cg_solve(bhs, [args.mass], tol=args.tol, maxiter=50000,
+                                      precision=prec, xs=xhs)
         e2e_ms.append(1e3 * (time.perf_counter() - t))
-        e2e_it.append(int(it[0]))
+        e2e_it.append(int(sum(it)))
     e2e_ms_step = statistics.mean(e2e_ms) if e2e_ms else None
     e2e_value = (FLOP_PER_SITE_ITER * Ve * statistics.mean(e2e_it) / (e2e_ms_step * 1e-3) / 1e9
                  if e2e_ms else None)
@@ -336,7 +350,8 @@ def run_ours(args):
     for kk, what in ((0, "t = D_oe r + beta t_old, |t|^2"),
                      (1, "p = r + beta p; r -= alpha (4m^2 p - D_eo t); x += alpha p; |r|^2, Re<r,p>")):
         ms_k, by_k = ctx.time_cg_kernel(kk, prec, nlaunch=100)
-        kern.append({"kernel": f"k_dslash CG kernel {kk + 1}: {what} ({args.precision}, links {args.links}, 1 RHS)",
+        kern.append({"kernel": f"k_dslash CG kernel {kk + 1}: {what} ({args.precision}, links {args.links}, "
+                               f"{nrhs} RHS)",
                      "key": f"cg_k{kk + 1}_{tag}", "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": by_k,
                      "achieved": by_k / (ms_k * 1e-3) / 1e9})
     dom = max(kern, key=lambda d: d["ms_per_launch"])
@@ -352,8 +367,12 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16),
-                        ("fp32", stag.STAG_FP32), ("fp16_half_vectors", stag.STAG_FP16 | stag.STAG_HALF_VECTORS)):
+        # single-source solves of the first source at the other precisions (with
+        # several sources: the FP64 and FP32 single-source references only)
+        cmp = ((("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16),
+                ("fp32", stag.STAG_FP32), ("fp16_half_vectors", stag.STAG_FP16 | stag.STAG_HALF_VECTORS))
+               if nrhs == 1 else (("fp64", stag.STAG_FP64), ("fp32", stag.STAG_FP32)))
+        for name, p in cmp:
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -366,14 +385,18 @@ def run_ours(args):
             extras[f"cg_{name}"] = {"ms": e0.elapsed_time(e1), "iters": int(it[0]),
                                     "reliable_updates": nu, "true_res": float(tr[0]),
                                     "status": stag.status_name(st)}
-        for name, p in (("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16)):
+        for name, p in ((("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16))
+                        if nrhs == 1 else ()):
             m, by = ctx.time_dslash(p, nlaunch=50)
             extras[f"dslash_{name}"] = {"ms": m, "GB/s": by / (m * 1e-3) / 1e9,
                                         "GFLOP/s": DSLASH_FLOP_PER_SITE * Ve / (m * 1e-3) / 1e9}
-        extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps)
+        # FP64 single-source time over the timed solve's time per source
+        extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps / nrhs)
 
     cpu = None
     if ws == 1 and rank == 0 and not args.no_extras:
+        if U is None:
+            U = Ud.cpu().numpy()
         g, it, dt = cpu_oracle_sample(L, U, b, args.mass, 12.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"{it} FP64 CG iterations of the CPU oracle on the same {L} field "
@@ -385,11 +408,13 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / PAPER_TX_CG_GFLOPS,
             "dtype": "f32" if args.precision == "fp32" else args.precision.replace("fp", "f"),
-            "data": "synthetic", "config": workload_config(L, args.mass, args.tol, args.precision, args.links),
-            "time_to_solution_ms": ms_step, "iters": iters[-1], "reliable_updates": updates[-1],
+            "data": "synthetic",
+            "config": workload_config(L, args.mass, args.tol, args.precision, args.links, nrhs),
+            "time_to_solution_ms": ms_step, "iters": iters[-1] if nrhs > 1 else iters[-1][0],
+            "reliable_updates": updates[-1],
             "true_res": max(res),
-            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve,
-                    "d2h_bytes_per_step": 48 * Ve, "ms_per_step": e2e_ms_step},
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve * nrhs,
+                    "d2h_bytes_per_step": 48 * Ve * nrhs, "ms_per_step": e2e_ms_step},
             "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -201,6 +201,17 @@ int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_upd
                      double *true_res);
 
 /*
+ * Loop counters of the most recent stag_cg_solve on this context (all its
+ * systems together): passes of the solve loop (each runs up to 4 CG
+ * iterations of every running system) and executions of the FP64
+ * reliable-update step (Sec. 3; each recomputes the residual of every system
+ * with an update due).  From them the kernels launched follow: 9 per pass and
+ * 5 per update step (4 with STAG_HALF_VECTORS).  Either pointer may be NULL.
+ * STAG_ERR_ARG before the first solve.
+ */
+int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps);
+
+/*
  * out_even = (4 m^2 - D_eo D_oe) in_even in FP64, with tmp_odd = D_oe in_even
  * and *dot = Re<in_even, out_even> (FP64, fixed-order reduction), for callers
  * that cannot allocate device memory (their memory is owned by another

@@ -381,7 +381,8 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
 // lanes; STAG_TMA = 1 turns the bulk-copied links on, = t lets the tuner
 // decide (default: off).
 int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArgs a1, DsArgs a2, bool tma_ok,
-                 int *l1_out, int *l2_out, int *tma_out) {
+                 int *l1_out, int *l2_out, int *tma_out, float *ms_out = nullptr) {
+  if (ms_out) *ms_out = -1.f;
   const int tma_lo = (tma_ok && c->tma_mode != 0) ? (c->tma_mode == 1 ? 1 : 0) : 0;
   const int tma_hi = (tma_ok && c->tma_mode != 0) ? 1 : 0;
   const char *force = getenv("STAG_LANES");
@@ -394,7 +395,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
   const int G = a1.ngroups;
   const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, G * 4 + tma_lo * 2 + tma_hi, c->dims[0], c->dims[1],
                     c->dims[2], c->dims[3]);
-  if (!fl) {
+  if (!fl && !ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     auto it = g_tune.find(key);
@@ -448,6 +449,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
   *tma_out = best / 4;
   *l1_out = 1 + (best / 2) % 2;
   *l2_out = 1 + best % 2;
+  if (ms_out) *ms_out = tot[best];
   if (!fl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int v = 100 * *tma_out + 10 * *l1_out + *l2_out;
@@ -535,9 +537,8 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   w.recon = recon;
   w.VP = VP;
   w.RP = RP;
-  if (prec == P64) w.NS = nsys >= 4 ? 4 : 1;
-  else w.NS = nsys >= 8 ? 8 : nsys >= 4 ? 4 : 1;
-  w.G = (nsys + w.NS - 1) / w.NS;
+  w.NS = 1;
+  w.G = nsys;
   w.NS64 = nsys >= 4 ? 4 : 1;
   w.G64 = (nsys + w.NS64 - 1) / w.NS64;
   const int Ve = c->Ve;
@@ -568,11 +569,8 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
   CK(cudaMemsetAsync(w.x64.data.p, 0, w.x64.data.n, c->stream));
   CK(cudaMemsetAsync(w.r.data.p, 0, w.r.data.n, c->stream));
-  // pick the thread mapping of the inner and the FP64 half operators
   const void *lo = nullptr;
   CKS(links_for(c, prec, &lo));
-  CKS(tune_lanes(c, prec, recon, VP, w.NS, w.G, nsys, lo, w.p.arg(), w.t.arg(), &w.lanes));
-  CKS(tune_lanes(c, P64, 0, P64, w.NS64, w.G64, nsys, c->links64.p, w.x64.arg(), w.t64.arg(), &w.lanes64));
   {
     // the two CG kernels with their own epilogues (state zeroed: alpha = beta = 0)
     DsArgs a = ds_base(c);
@@ -590,6 +588,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a.links_tile = w.links_tile;
     a.ntile = link_tiles(c->Ve);
     const bool rec = (VP == w.RP);
+    const int epi1 = rec ? EPI_CG_K1R : EPI_CG_K1;
     DsArgs a2 = a;
     a.par_out = 1;
     a.in = rec ? w.r.arg() : w.p.arg();
@@ -597,11 +596,62 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a2.par_out = 0;
     a2.in = w.t.arg();
     a2.center = w.p.arg();
-    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, a, a2, tma_ok, &w.lanes_k1,
-                     &w.lanes_k2, &w.tma));
-    CKS(cg_blocks(c, prec, recon, VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
+    // Systems per thread of the CG kernels.  NS = 1 gives every system its own
+    // blocks; the blocks of one chunk (consecutive in the grid) run together and
+    // share its links through L2.  NS = 4 or 8 holds the links in registers
+    // for all the thread's systems, at the price of registers (occupancy).
+    // Several systems: the candidates are timed (kernel pair, tune_cg_pair)
+    // and the choice cached; STAG_NS = 1, 4 or 8 fixes it.
+    std::vector<int> cands{1};
+    if (nsys >= 4) cands.push_back(4);
+    if (nsys >= 8 && prec != P64) cands.push_back(8);
+    const char *fns = getenv("STAG_NS");
+    if (fns && (fns[0] == '1' || fns[0] == '4' || fns[0] == '8') && fns[1] == 0) {
+      const int f = fns[0] - '0';
+      if (f <= nsys && !(f == 8 && prec == P64)) cands.assign(1, f);
+    }
+    int best_ns = cands[0];
+    if (cands.size() > 1) {
+      const TuneKey nkey(prec, recon, VP, 2000 + nsys, tma_ok ? 1 : 0, c->dims[0], c->dims[1], c->dims[2],
+                         c->dims[3]);
+      bool cached = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
+        auto it = g_tune.find(nkey);
+        if (it != g_tune.end()) {
+          best_ns = it->second;
+          cached = true;
+        }
+      }
+      if (!cached) {
+        float best_ms = 1e30f;
+        for (int ns : cands) {
+          a.ngroups = a2.ngroups = (nsys + ns - 1) / ns;
+          int l1, l2, t;
+          float ms = -1.f;
+          CKS(tune_cg_pair(c, prec, recon, VP, ns, epi1, a, a2, tma_ok && ns == 1, &l1, &l2, &t, &ms));
+          if (ms >= 0.f && ms < best_ms) {
+            best_ms = ms;
+            best_ns = ns;
+          }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[nkey] = best_ns;
+        tune_cache_store(nkey, best_ns);
+      }
+    }
+    w.NS = best_ns;
+    w.G = (nsys + w.NS - 1) / w.NS;
+    a.ngroups = a2.ngroups = w.G;
+    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, epi1, a, a2, tma_ok && w.NS == 1, &w.lanes_k1, &w.lanes_k2,
+                     &w.tma));
+    CKS(cg_blocks(c, prec, recon, VP, w.NS, epi1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
     CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, w.tma, &w.nbx_k2));
   }
+  // the thread mapping of the plain inner and the FP64 half operators
+  CKS(tune_lanes(c, prec, recon, VP, w.NS, w.G, nsys, lo, w.p.arg(), w.t.arg(), &w.lanes));
+  CKS(tune_lanes(c, P64, 0, P64, w.NS64, w.G64, nsys, c->links64.p, w.x64.arg(), w.t64.arg(), &w.lanes64));
   return STAG_OK;
 }
 
@@ -1454,6 +1504,14 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
   return STAG_OK;
 }
 
+int stag_solve_counters(const stag_ctx *c, int *loop_passes, int *update_steps) {
+  if (!c || c->last_nsys <= 0) return STAG_ERR_ARG;
+  const int *hf = (const int *)c->w.h_flags.p;
+  if (loop_passes) *loop_passes = hf[2];
+  if (update_steps) *update_steps = hf[5];
+  return STAG_OK;
+}
+
 int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, double *ms_per_launch,
                         double *bytes_per_launch) {
   if (!c) return STAG_ERR_ARG;
@@ -1530,6 +1588,7 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
     //   first kernel: t_old read (recurrence) or p_old gathered (gather form), t written
     //   second kernel: p read and written, r and x_lo read and written
     const double per = (kernel == 0) ? (2.0 * vb + rb) : (3.0 * vb + 4.0 * rb);
+    // algorithmic: the links once, whatever the grouping of the systems
     *bytes_per_launch = (double)c->Ve * (8.0 * lb + w.nsys * per);
   }
   return STAG_OK;

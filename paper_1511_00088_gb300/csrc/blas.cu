@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int n
     c.flags[2] = passes;
     if (passes > c.flags[3]) running = 0;
   }
+  if (fin == FIN_RESID) c.flags[5] += 1;  // executions of the reliable-update step
   c.flags[0] = running;
   c.flags[1] = upd;
   if (c.use_graph_cond) {

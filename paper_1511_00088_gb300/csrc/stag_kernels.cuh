@@ -107,7 +107,8 @@ struct Ctl {
   double *partials;      // [nsys][NVMAX][pstride]   one per block of the reducing kernel
   unsigned *all_ticket;  // [1] finalize blocks done
   int *flags;            // [0] any system running, [1] any reliable update due,
-                         // [2] passes of the norm kernel this solve, [3] cap on [2]
+                         // [2] passes of the norm finalize this solve, [3] cap on [2],
+                         // [4] a bulk-copy wait gave up, [5] reliable-update steps run
   int pstride;           // partial slots per (system, value)
   int use_graph_cond;    // call cudaGraphSetConditional on the handles below
   cudaGraphConditionalHandle h_loop, h_update;

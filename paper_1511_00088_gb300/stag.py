@@ -78,6 +78,7 @@ def load():
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
+            "stag_solve_counters": (I, [P, P, P]),
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_force": (I, [P, P, P, P]),
@@ -172,6 +173,13 @@ def stag_time_dslash(ctx, precision, nlaunch):
     by = ctypes.c_double(0.0)
     st = load().stag_time_dslash(ctx, int(precision), int(nlaunch), ctypes.byref(ms), ctypes.byref(by))
     return st, ms.value, by.value
+
+
+def stag_solve_counters(ctx):
+    passes = ctypes.c_int(0)
+    ups = ctypes.c_int(0)
+    st = load().stag_solve_counters(ctx, ctypes.byref(passes), ctypes.byref(ups))
+    return st, passes.value, ups.value
 
 
 def stag_time_cg_kernel(ctx, precision, kernel, nlaunch):
@@ -359,6 +367,12 @@ class Context:
         st, ms, by = stag_time_dslash(self.h, precision, nlaunch)
         self._check(st)
         return ms, by
+
+    def solve_counters(self):
+        """(loop passes, reliable-update steps) of the most recent solve."""
+        st, passes, ups = stag_solve_counters(self.h)
+        self._check(st)
+        return passes, ups
 
     def time_cg_kernel(self, kernel, precision=STAG_FP32, nlaunch=50):
         """(ms per launch, algorithmic bytes per launch) of CG kernel 0 or 1."""
