@@ -309,6 +309,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    form = ctx.solve_form()
     ms_step = total_ms / args.steps
     flops_step = FLOP_PER_SITE_ITER * Ve * statistics.mean(sum(i) for i in iters)
     if dist:
@@ -416,6 +417,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve * nrhs,
                     "d2h_bytes_per_step": 48 * Ve * nrhs, "ms_per_step": e2e_ms_step},
             "gpu_launches": launches,
+            "launch_form": form,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -212,6 +212,17 @@ int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_upd
 int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps);
 
 /*
+ * The launch form the autotuner chose for the CG kernels of the most recent
+ * solve (or timing call): out[0] systems per thread, out[1] system groups,
+ * out[2] / out[3] lanes per site of the first / second kernel, out[4] link
+ * path (0 plane layout, 1 tiled through shared memory, 2 tiled into
+ * registers), out[5] 1 when the links persist in L2 during the solve.
+ * Implementation detail of this library (the paper has no counterpart), for
+ * reports.  STAG_ERR_ARG before the first solve.
+ */
+int stag_solve_form(const stag_ctx *ctx, int out[6]);
+
+/*
  * out_even = (4 m^2 - D_eo D_oe) in_even in FP64, with tmp_odd = D_oe in_even
  * and *dot = Re<in_even, out_even> (FP64, fixed-order reduction), for callers
  * that cannot allocate device memory (their memory is owned by another

@@ -121,7 +121,8 @@ struct Work {
   int lanes = 1, lanes64 = 1;  // lanes per site of the inner / FP64 half operator (tuned)
   int lanes_k1 = 1, lanes_k2 = 1;  // lanes of the two CG kernels (tuned with their epilogues)
   int nbx_k1 = 0, nbx_k2 = 0;      // blocks per system group of the two CG kernels
-  int tma = 0;                     // the CG kernels read bulk-copied tiled links
+  int tma = 0;                     // link path of the CG kernels (DsArgs::tma)
+  int l2p = 0;                     // their links persist in L2 during a solve
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
@@ -171,7 +172,14 @@ struct stag_ctx {
   bool pdl = true;  // CG kernels launched as programmatic dependents of their predecessors
   bool fold = true;     // each CG kernel finishes its predecessor's reduction itself
   bool persist = true;  // CG kernels launched as one wave of resident blocks
-  int tma_mode = 0;     // bulk-copied links in the single-system CG kernels: 0 off, 1 on, -1 tuned
+  int tma_modes = 0b101;  // link paths (bit t: DsArgs::tma = t) the tuner may choose for one system
+  // L2 residency of the inner-precision links during a solve: the CG kernels
+  // mark them as an access-policy window whose lines persist in L2 (the rest
+  // of their traffic streams), so of the two passes over the links per
+  // iteration most hit L2; the persisting lines are released after the solve
+  bool l2persist = true;  // the device supports it and it is not switched off
+  int l2_modes = 0b11;    // bit p: the tuner may choose persisting links p (STAG_L2PERSIST = 0 or 1 fixes it)
+  size_t l2_max_persist = 0, l2_max_window = 0;
   DevBuf links_canon;  // [4][V][3][3] FP64, kept for lazy reduced-precision copies
   DevBuf links64;
   DevBuf links_lo[4][2];
@@ -296,6 +304,21 @@ int links_tile_for(stag_ctx *c, int P, const void **out) {
   return STAG_OK;
 }
 
+// the L2 window of the CG kernels' links for link path tma (DsArgs::tma)
+void set_l2_window(stag_ctx *c, int P, int tma, int on, DsArgs &a) {
+  a.l2_base = nullptr;
+  a.l2_bytes = 0;
+  a.l2_hit = 0.f;
+  if (!c->l2persist || !on) return;
+  const int rc = (P != P64 && (c->flags & STAG_RECON12)) ? 1 : 0;
+  const DevBuf &b = (P == P64) ? c->links64 : (tma ? c->links_tile[P][rc] : c->links_lo[P][rc]);
+  if (!b.p || b.n == 0) return;
+  a.l2_base = b.p;
+  a.l2_bytes = b.n < c->l2_max_window ? b.n : c->l2_max_window;
+  const double h = (double)c->l2_max_persist / (double)a.l2_bytes;
+  a.l2_hit = h < 1.0 ? (float)h : 1.f;
+}
+
 int link_recon(const stag_ctx *c, int P) { return (P != P64 && (c->flags & STAG_RECON12)) ? 1 : 0; }
 
 Ctl no_ctl() {
@@ -363,7 +386,7 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
   const void *k = nullptr;
   CK(launch_dslash(LP, recon, VP, VP, NS, EPI, lanes, 0, c->stream, none, &k));
   int per_sm = 0, nsm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, DS_BT, tma ? tma_smem_bytes(LP, recon, lanes) : 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, DS_BT, tma == 1 ? tma_smem_bytes(LP, recon, lanes) : 0));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   int n = per_sm * nsm / G;
   if (n < 1) n = 1;
@@ -373,86 +396,114 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
 
 // The launch form of the two CG kernels, chosen together: lanes per site of
 // each (1 or 2) and, where allowed (tma_ok: one system, reduced-precision
-// links), whether both read their links through bulk copies.  Each candidate
+// links), the link path of both (DsArgs::tma, among c->tma_modes); whether
+// their links persist in L2 follows a rule (below).  Each candidate
 // runs 20 alternating launch pairs with the solver's grids, twice (the second
 // sweep in reverse order), and the fastest total wins: the iteration
 // alternates the two kernels, each starting on the cache state the other
-// leaves.  Cached as 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2 fixes the
-// lanes; STAG_TMA = 1 turns the bulk-copied links on, = t lets the tuner
-// decide (default: off).
+// leaves.  Cached as 1000 l2p + 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2
+// fixes the lanes.
+struct CgForm {
+  int tma = 0, l1 = 1, l2 = 1, l2p = 0;  // link path, lanes of the two kernels, L2-persisting links
+};
+
 int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArgs a1, DsArgs a2, bool tma_ok,
-                 int *l1_out, int *l2_out, int *tma_out, float *ms_out = nullptr) {
+                 CgForm *out, float *ms_out = nullptr) {
   if (ms_out) *ms_out = -1.f;
-  const int tma_lo = (tma_ok && c->tma_mode != 0) ? (c->tma_mode == 1 ? 1 : 0) : 0;
-  const int tma_hi = (tma_ok && c->tma_mode != 0) ? 1 : 0;
+  const int modes = tma_ok ? c->tma_modes : 1;  // bit t: link path t allowed
+  // persisting links (bit p of l2modes: p allowed): by rule, not by timing --
+  // short timings favoured them where whole solves ran slower.  On for one
+  // system whose links fit the persisting set-aside to within 25 % (20^3 x 64
+  // reconstruct-12 FP32: 98 MB against 84.7 MB, 10 % faster solves); off where
+  // they do not fit (full FP32 links, 147 MB: 6 % slower) and for several
+  // systems, whose vectors need the rest of L2 (16 sources: 27 % slower).
+  int l2modes = 1;
+  if (c->l2persist) {
+    if (c->l2_modes != 0b11) {
+      l2modes = c->l2_modes;
+    } else {
+      const int rc = (LP != P64 && recon) ? 1 : 0;
+      const double lb = (double)cplx_bytes(LP) * (rc ? 6 : 9) * 8.0 * c->Ve;
+      l2modes = (a1.nsys == 1 && lb <= 1.25 * (double)c->l2_max_persist) ? 0b10 : 0b01;
+    }
+  }
   const char *force = getenv("STAG_LANES");
   const int fl = (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) ? force[0] - '0' : 0;
-  if (fl && tma_lo == tma_hi) {
-    *l1_out = *l2_out = fl;
-    *tma_out = tma_lo;
+  std::vector<CgForm> cand;
+  for (int p = 0; p < 2; ++p)
+    for (int t = 0; t < 3; ++t)
+      for (int l1 = 1; l1 <= 2; ++l1)
+        for (int l2 = 1; l2 <= 2; ++l2)
+          if ((l2modes >> p & 1) && (modes >> t & 1) && (!fl || (l1 == fl && l2 == fl))) {
+            CgForm f;
+            f.tma = t;
+            f.l1 = l1;
+            f.l2 = l2;
+            f.l2p = p;
+            cand.push_back(f);
+          }
+  if (cand.size() == 1 && !ms_out) {
+    *out = cand[0];
     return STAG_OK;
   }
   const int G = a1.ngroups;
-  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, G * 4 + tma_lo * 2 + tma_hi, c->dims[0], c->dims[1],
+  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, (G * 8 + modes) * 4 + l2modes, c->dims[0], c->dims[1],
                     c->dims[2], c->dims[3]);
   if (!fl && !ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *tma_out = it->second / 100;
-      *l1_out = (it->second / 10) % 10;
-      *l2_out = it->second % 10;
+      out->l2p = it->second / 1000;
+      out->tma = (it->second / 100) % 10;
+      out->l1 = (it->second / 10) % 10;
+      out->l2 = it->second % 10;
       return STAG_OK;
     }
   }
-  // candidates q = 4 tma + 2 (l1 - 1) + (l2 - 1)
-  std::vector<int> cand;
-  for (int t = tma_lo; t <= tma_hi; ++t)
-    for (int l1 = 1; l1 <= 2; ++l1)
-      for (int l2 = 1; l2 <= 2; ++l2)
-        if (!fl || (l1 == fl && l2 == fl)) cand.push_back(4 * t + 2 * (l1 - 1) + (l2 - 1));
-  int nb1[8], nb2[8];
-  for (int q : cand) {
-    const int t = q / 4, l1 = 1 + (q / 2) % 2, l2 = 1 + q % 2;
+  const int nc = (int)cand.size();
+  std::vector<int> nb1(nc), nb2(nc);
+  for (int q = 0; q < nc; ++q) {
     int n = 0;
-    CKS(cg_blocks(c, LP, recon, VP, NS, EPI1, l1, G, t, &n));
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI1, cand[q].l1, G, cand[q].tma, &n));
     nb1[q] = n * G;
-    CKS(cg_blocks(c, LP, recon, VP, NS, EPI_CG_K2, l2, G, t, &n));
+    CKS(cg_blocks(c, LP, recon, VP, NS, EPI_CG_K2, cand[q].l2, G, cand[q].tma, &n));
     nb2[q] = n * G;
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float tot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int nc = (int)cand.size();
+  std::vector<float> tot(nc, 0.f);
   for (int o = 0; o < 2 * nc; ++o) {
-    const int q = cand[o < nc ? o : 2 * nc - 1 - o];
-    const int t = q / 4, l1 = 1 + (q / 2) % 2, l2 = 1 + q % 2;
-    a1.tma = a2.tma = t;
+    const int q = o < nc ? o : 2 * nc - 1 - o;
+    const CgForm &f = cand[q];
+    a1.tma = a2.tma = f.tma;
+    set_l2_window(c, LP, f.tma, f.l2p, a1);
+    set_l2_window(c, LP, f.tma, f.l2p, a2);
     for (int i = 0; i < 22; ++i) {
       if (i == 2) CK(cudaEventRecord(e0, c->stream));
-      CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, l1, nb1[q], c->stream, a1));
-      CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, l2, nb2[q], c->stream, a2));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, f.l1, nb1[q], c->stream, a1));
+      CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, f.l2, nb2[q], c->stream, a2));
     }
     CK(cudaEventRecord(e1, c->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     tot[q] += ms;
+    // each candidate starts without persisting lines
+    if (c->l2persist) cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int best = cand[0];
-  for (int q : cand)
+  int best = 0;
+  for (int q = 1; q < nc; ++q)
     if (tot[q] < tot[best]) best = q;
-  *tma_out = best / 4;
-  *l1_out = 1 + (best / 2) % 2;
-  *l2_out = 1 + best % 2;
+  *out = cand[best];
   if (ms_out) *ms_out = tot[best];
   if (!fl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    const int v = 100 * *tma_out + 10 * *l1_out + *l2_out;
+    const int v = 1000 * out->l2p + 100 * out->tma + 10 * out->l1 + out->l2;
     g_tune[key] = v;
     tune_cache_store(key, v);
   }
@@ -582,7 +633,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     a.fin = FIN_NONE;
     a.aux = w.r.arg();
     a.xlo = w.x.arg();
-    const bool tma_ok = (w.NS == 1 && prec != P64 && c->tma_mode != 0);
+    const bool tma_ok = (w.NS == 1 && prec != P64 && c->tma_modes != 1);
     w.links_tile = nullptr;
     if (tma_ok) CKS(links_tile_for(c, prec, &w.links_tile));
     a.links_tile = w.links_tile;
@@ -628,9 +679,9 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
         float best_ms = 1e30f;
         for (int ns : cands) {
           a.ngroups = a2.ngroups = (nsys + ns - 1) / ns;
-          int l1, l2, t;
+          CgForm f;
           float ms = -1.f;
-          CKS(tune_cg_pair(c, prec, recon, VP, ns, epi1, a, a2, tma_ok && ns == 1, &l1, &l2, &t, &ms));
+          CKS(tune_cg_pair(c, prec, recon, VP, ns, epi1, a, a2, tma_ok && ns == 1, &f, &ms));
           if (ms >= 0.f && ms < best_ms) {
             best_ms = ms;
             best_ns = ns;
@@ -644,8 +695,12 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
     w.NS = best_ns;
     w.G = (nsys + w.NS - 1) / w.NS;
     a.ngroups = a2.ngroups = w.G;
-    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, epi1, a, a2, tma_ok && w.NS == 1, &w.lanes_k1, &w.lanes_k2,
-                     &w.tma));
+    CgForm form;
+    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, epi1, a, a2, tma_ok && w.NS == 1, &form));
+    w.tma = form.tma;
+    w.lanes_k1 = form.l1;
+    w.lanes_k2 = form.l2;
+    w.l2p = form.l2p;
     CKS(cg_blocks(c, prec, recon, VP, w.NS, epi1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
     CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, w.tma, &w.nbx_k2));
   }
@@ -712,6 +767,7 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.tma = w.tma;
   a.links_tile = w.links_tile;
   a.ntile = link_tiles(c->Ve);
+  set_l2_window(c, w.prec, w.tma, w.l2p, a);
   // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2) -> alpha
   a.par_out = 1;
   a.in = (w.VP == w.RP) ? w.r.arg() : w.p.arg();
@@ -772,6 +828,7 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
   a.tma = w.tma;
   a.links_tile = w.links_tile;
   a.ntile = link_tiles(c->Ve);
+  set_l2_window(c, w.prec, w.tma, w.l2p, a);
   int cur = 0;  // buffer of the current states
   for (int u = 0; u < unroll; ++u) {
     // K1: t = D_oe (r + beta p_old); |t|^2 (and |p|^2); folds the previous K2's norms
@@ -1025,6 +1082,10 @@ int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[])
   for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
   CK(cudaStreamSynchronize(c->stream));
   c->last_nsys = nsys;
+  // the solve's persisting L2 lines back to normal (the next user of L2, or a
+  // flush between timed solves, may evict them)
+  if (c->l2persist) cudaCtxResetPersistingL2Cache();
+  cudaGetLastError();
   if (hf[4] != 0) {
     c->err = "a CG kernel gave up waiting for its bulk-copied links; the solution is void";
     return STAG_ERR_CUDA;
@@ -1313,14 +1374,38 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   const char *persist = getenv("STAG_PERSIST");
   c->persist = !(persist && persist[0] == '0');
   const char *tma = getenv("STAG_TMA");
-  // measured slower than the register path at FP32 and FP16 (shared memory
-  // caps the sites in flight per SM below what the registers hold), so opt-in
-  c->tma_mode = (tma && tma[0] == '1') ? 1 : (tma && tma[0] == 't') ? -1 : 0;
+  // STAG_TMA = 0, 1 or 2 fixes the link path of the single-system CG kernels,
+  // t lets the tuner try all three; by default it tries 0 and 2 (the bulk
+  // copies through shared memory, 1, measured slower at FP32 and FP16: shared
+  // memory caps the sites in flight per SM below what the registers hold)
+  if (tma && (tma[0] == '0' || tma[0] == '1' || tma[0] == '2') && tma[1] == 0) c->tma_modes = 1 << (tma[0] - '0');
+  else if (tma && tma[0] == 't' && tma[1] == 0) c->tma_modes = 0b111;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return STAG_ERR_CUDA;
+  }
+  {
+    const char *l2p = getenv("STAG_L2PERSIST");
+    c->l2persist = !(l2p && l2p[0] == '0');
+    if (l2p && l2p[0] == '1') c->l2_modes = 0b10;
+    int maxp = 0, maxw = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, c->device) != cudaSuccess)
+      maxp = maxw = 0;
+    cudaGetLastError();
+    if (c->l2persist && maxp > 0 && maxw > 0) {
+      // the context's set-aside for persisting lines (released with the context)
+      size_t cur = 0;
+      if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur < (size_t)maxp &&
+          cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) != cudaSuccess)
+        maxp = 0;
+      cudaGetLastError();
+      c->l2_max_persist = (size_t)maxp;
+      c->l2_max_window = (size_t)maxw;
+    }
+    if (c->l2_max_persist == 0) c->l2persist = false;
   }
   *out = c;
   return STAG_OK;
@@ -1504,6 +1589,18 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
   return STAG_OK;
 }
 
+int stag_solve_form(const stag_ctx *c, int out[6]) {
+  if (!c || !out || c->w.nsys <= 0) return STAG_ERR_ARG;
+  const Work &w = c->w;
+  out[0] = w.NS;
+  out[1] = w.G;
+  out[2] = w.lanes_k1;
+  out[3] = w.lanes_k2;
+  out[4] = w.tma;
+  out[5] = w.l2p;
+  return STAG_OK;
+}
+
 int stag_solve_counters(const stag_ctx *c, int *loop_passes, int *update_steps) {
   if (!c || c->last_nsys <= 0) return STAG_ERR_ARG;
   const int *hf = (const int *)c->w.h_flags.p;
@@ -1539,6 +1636,7 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   a1.tma = w.tma;
   a1.links_tile = w.links_tile;
   a1.ntile = link_tiles(c->Ve);
+  set_l2_window(c, w.prec, w.tma, w.l2p, a1);
   DsArgs a2 = a1;
   a1.par_out = 1;
   const int epi1 = (w.VP == w.RP) ? EPI_CG_K1R : EPI_CG_K1;
@@ -1578,6 +1676,8 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   }
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
+  if (c->l2persist) cudaCtxResetPersistingL2Cache();
+  cudaGetLastError();
   if (st != STAG_OK) return st;
   *ms_per_launch = tot / nlaunch;
   if (bytes_per_launch) {

@@ -5,13 +5,21 @@
 
 namespace stag {
 // one instantiation of the half operator: launch it, or (kptr) return it; with
-// a.tma the bulk-copied-links variant where it exists
+// a.tma = 1 or 2 the tiled-links variant where it exists
 template <int LP_, int RC_, int VP_, int OP_, int NS_, int EPI_, int L_>
 cudaError_t ds_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **kptr) {
   constexpr bool CAN_TMA =
       NS_ == 1 && LP_ != P64 && (EPI_ == EPI_CG_K1 || EPI_ == EPI_CG_K1R || EPI_ == EPI_CG_K2);
   if constexpr (CAN_TMA) {
-    if (a.tma) {
+    if (a.tma == 2) {
+      auto k = k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, L_, 2>;
+      if (kptr) {
+        *kptr = (const void *)k;
+        return cudaSuccess;
+      }
+      return launch_ex_full(k, nblocks, DS_BT, 0u, st, a.pdl != 0, a.l2_base, a.l2_bytes, a.l2_hit, a);
+    }
+    if (a.tma == 1) {
       auto k = k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, L_, 1>;
       const unsigned smem = tma_smem_bytes(LP_, RC_, L_);
       static bool attr_set = false;  // benign race: setting it twice is harmless
@@ -24,7 +32,7 @@ cudaError_t ds_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **k
         *kptr = (const void *)k;
         return cudaSuccess;
       }
-      return launch_ex_smem(k, nblocks, DS_BT, smem, st, a.pdl != 0, a);
+      return launch_ex_full(k, nblocks, DS_BT, smem, st, a.pdl != 0, a.l2_base, a.l2_bytes, a.l2_hit, a);
     }
   }
   auto k = k_dslash<LP_, RC_, VP_, OP_, NS_, EPI_, DS_BT, L_>;
@@ -32,7 +40,7 @@ cudaError_t ds_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **k
     *kptr = (const void *)k;
     return cudaSuccess;
   }
-  return launch_ex(k, nblocks, DS_BT, st, a.pdl != 0, a);
+  return launch_ex_full(k, nblocks, DS_BT, 0u, st, a.pdl != 0, a.l2_base, a.l2_bytes, a.l2_hit, a);
 }
 }  // namespace stag
 

@@ -20,19 +20,38 @@ constexpr int BLAS_BT = 256;  // threads per block of the BLAS-1 kernels
 // previous kernel in the stream drains, and must reach grid_dep_wait() before
 // it reads or writes anything that kernel touches.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_ex_smem(void (*k)(KArgs...), int nblocks, int bt, unsigned smem, cudaStream_t st,
-                                  bool pdl, Args &&...args) {
+inline cudaError_t launch_ex_full(void (*k)(KArgs...), int nblocks, int bt, unsigned smem, cudaStream_t st,
+                                  bool pdl, const void *l2_base, size_t l2_bytes, float l2_hit, Args &&...args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblocks);
   cfg.blockDim = dim3((unsigned)bt);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
+  unsigned n = 0;
+  if (pdl) {
+    at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  if (l2_bytes > 0) {
+    // a fraction l2_hit of the window's lines persists in L2 across kernels
+    at[n].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[n].val.accessPolicyWindow.base_ptr = const_cast<void *>(l2_base);
+    at[n].val.accessPolicyWindow.num_bytes = l2_bytes;
+    at[n].val.accessPolicyWindow.hitRatio = l2_hit;
+    at[n].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[n].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    ++n;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = n;
   return cudaLaunchKernelEx(&cfg, k, static_cast<Args &&>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex_smem(void (*k)(KArgs...), int nblocks, int bt, unsigned smem, cudaStream_t st,
+                                  bool pdl, Args &&...args) {
+  return launch_ex_full(k, nblocks, bt, smem, st, pdl, nullptr, 0, 0.f, static_cast<Args &&>(args)...);
 }
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_ex(void (*k)(KArgs...), int nblocks, int bt, cudaStream_t st, bool pdl,

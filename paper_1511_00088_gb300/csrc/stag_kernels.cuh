@@ -145,9 +145,15 @@ struct DsArgs {
   const double *fold_partials;
   SysState *st_out;
   // tma != 0 (single-system CG kernels): the links are read from links_tile
-  // (the tiled site-owned copy, ntile tiles per parity) through shared memory
+  // (the tiled site-owned copy, ntile tiles per parity): 1 through shared
+  // memory (bulk copies), 2 straight into registers
   int tma, ntile;
   const void *links_tile;
+  // host side only (launch attribute): l2_bytes > 0 marks [l2_base, l2_base +
+  // l2_bytes) as an L2 access-policy window, a fraction l2_hit of it persisting
+  const void *l2_base;
+  size_t l2_bytes;
+  float l2_hit;
 };
 
 struct BlasArgs {
@@ -671,14 +677,19 @@ __global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys, cons
 // thread's directions are all in flight together (measured: 27 us instead of
 // 34 us for D_oe at 20^3 x 64, FP32).
 // (The FP64 kernels are bound by GB300's FP64 pipe and keep 4 blocks per SM.)
-// TMA (one system, FP32/FP16/BF16 links): the links come from the tiled
-// site-owned copy through a two-stage ring in dynamic shared memory; one
-// thread issues each chunk's bulk copy a round ahead (the first before the
-// wait for the predecessor grid, as the links never change during a solve),
-// so the link stream needs no registers and overlaps the arithmetic.
+// TMA (one system, FP32/FP16/BF16 links) selects where the links come from:
+//  0: the plane layout [parity][mu][element][Ve] (the backward links gathered
+//     at the neighbours);
+//  1: the tiled site-owned copy through a two-stage ring in dynamic shared
+//     memory; one thread issues each chunk's bulk copy a round ahead (the first
+//     before the wait for the predecessor grid, as the links never change
+//     during a solve), so the link stream needs no registers;
+//  2: the tiled site-owned copy loaded straight into registers: a warp's 8
+//     links then lie in one contiguous block of 32 LT-site rows (fewer DRAM
+//     pages per load round than 48 planes of the plane layout).
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES, int TMA = 0>
 __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a) {
-  static_assert(!TMA || (NS == 1 && LP != P64), "bulk-copied links: one system, reduced-precision links");
+  static_assert(!TMA || (NS == 1 && LP != P64), "tiled links: one system, reduced-precision links");
   typedef typename Tr<LP>::R R;
   typedef typename Tr<LP>::S2 LS2;
   constexpr int RP = (LP == P64) ? P64 : P32;  // precision of the residual r
@@ -717,7 +728,7 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
                      ((long long)a.par_out * a.ntile + (long long)(bx0 + q * nbx) * (SPB / LT)) * (8 * NEL * LT);
     bulk_copy_g2s(stage_mem + (q % NSTG) * CHUNK, src, CHUNK, &stage_bar[q % NSTG]);
   };
-  if (TMA) {
+  if (TMA == 1) {
     if (threadIdx.x == 0) {
       for (int q = 0; q < NSTG; ++q) mbar_init(&stage_bar[q], 1);
       fence_mbar_init();
@@ -757,8 +768,8 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
 
   int round = 0;
   for (int bx = bx0; bx < nchunk; bx += nbx, ++round) {
-  const LS2 *lsm = nullptr;  // this round's links in shared memory (TMA)
-  if (TMA) {
+  const LS2 *lsm = nullptr;  // this round's links in shared memory (TMA == 1)
+  if (TMA == 1) {
     if (round > 0) __syncthreads();  // every thread is done with the stage read last round
     if (threadIdx.x == 0 && round + NSTG - 1 < nmine) {
       fence_proxy_async_smem();
@@ -827,11 +838,16 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a
 #pragma unroll
       for (int dd = 0; dd < DPL; ++dd) {
         const int mu = lane * DPL + dd;
-        if (TMA) {
+        if (TMA == 1) {
           const int i = (int)threadIdx.x / LANES;  // site within the chunk
           const LS2 *q = lsm + (i / LT) * (8 * NEL * LT) + i % LT;
           load_link_at<LP, RECON, true>(q + mu * (NEL * LT), LT, uf[dd]);
           load_link_at<LP, RECON, true>(q + (4 + mu) * (NEL * LT), LT, ub[dd]);
+        } else if (TMA == 2) {
+          const LS2 *q = reinterpret_cast<const LS2 *>(a.links_tile) +
+                         ((long long)P * a.ntile + s / LT) * (8 * NEL * LT) + s % LT;
+          load_link_at<LP, RECON, false>(q + mu * (NEL * LT), LT, uf[dd]);
+          load_link_at<LP, RECON, false>(q + (4 + mu) * (NEL * LT), LT, ub[dd]);
         } else {
           load_link<LP, RECON>(a.links, Ve, P, mu, s, uf[dd]);
           load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sb[dd], ub[dd]);

@@ -79,6 +79,7 @@ def load():
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_counters": (I, [P, P, P]),
+            "stag_solve_form": (I, [P, P]),
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_force": (I, [P, P, P, P]),
@@ -180,6 +181,12 @@ def stag_solve_counters(ctx):
     ups = ctypes.c_int(0)
     st = load().stag_solve_counters(ctx, ctypes.byref(passes), ctypes.byref(ups))
     return st, passes.value, ups.value
+
+
+def stag_solve_form(ctx):
+    out = (ctypes.c_int * 6)()
+    st = load().stag_solve_form(ctx, out)
+    return st, list(out)
 
 
 def stag_time_cg_kernel(ctx, precision, kernel, nlaunch):
@@ -373,6 +380,13 @@ class Context:
         st, passes, ups = stag_solve_counters(self.h)
         self._check(st)
         return passes, ups
+
+    def solve_form(self):
+        """The autotuner's launch form of the CG kernels of the last solve."""
+        st, f = stag_solve_form(self.h)
+        self._check(st)
+        return {"systems_per_thread": f[0], "groups": f[1], "lanes_k1": f[2], "lanes_k2": f[3],
+                "link_path": ("planes", "tiled_smem", "tiled")[f[4]], "l2_persisting_links": bool(f[5])}
 
     def time_cg_kernel(self, kernel, precision=STAG_FP32, nlaunch=50):
         """(ms per launch, algorithmic bytes per launch) of CG kernel 0 or 1."""

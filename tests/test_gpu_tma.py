@@ -1,11 +1,12 @@
-"""The single-system CG kernels with bulk-copied links (tiled site-owned link
-copy staged through shared memory) against the register path and the oracle.
+"""The single-system CG kernels reading the tiled site-owned link copy -- staged
+through shared memory by bulk copies (link path 1) or loaded straight into
+registers (link path 2) -- against the plane-layout path (0) and the oracle.
 
-The two paths read the same link values and do the same arithmetic per site;
-their one-wave grids differ in size (shared memory limits the bulk-copy
-variant's residency), so the reduction order differs and the comparison is at
-the solve tolerance: both reach ||b - A x|| / ||b|| <= 1e-10 by the oracle's
-own residual, and agree to the accuracy the condition number allows.
+The paths read the same link values and do the same arithmetic per site; their
+one-wave grids may differ in size (shared memory limits path 1's residency), so
+the reduction order may differ and the comparison is at the solve tolerance:
+both reach ||b - A x|| / ||b|| <= 1e-10 by the oracle's own residual, and agree
+to the accuracy the condition number allows.
 """
 import os
 
@@ -47,12 +48,13 @@ def solve_with(L, U, b, m, prec, recon, tma, lanes):
 @pytest.mark.parametrize("L", [(2, 2, 2, 2), (4, 2, 6, 8), (6, 6, 6, 12), (8, 8, 8, 16)])
 @pytest.mark.parametrize("recon", [False, True])
 @pytest.mark.parametrize("lanes", [1, 2])
-def test_bulk_copied_links_match(L, recon, lanes):
+@pytest.mark.parametrize("path", [1, 2])
+def test_tiled_links_match(L, recon, lanes, path):
     V = synth.volume(L)
     U = synth.random_links(L, 0.4, 71)
     b = synth.gaussian_vector(V // 2, 72)
     m = 0.05
-    x1, it1, tr1 = solve_with(L, U, b, m, stag.STAG_FP32, recon, 1, lanes)
+    x1, it1, tr1 = solve_with(L, U, b, m, stag.STAG_FP32, recon, path, lanes)
     x0, it0, tr0 = solve_with(L, U, b, m, stag.STAG_FP32, recon, 0, lanes)
     for x, tr in ((x1, tr1), (x0, tr0)):
         t = oracle.true_residual(L, U, m, b, x)
@@ -63,13 +65,14 @@ def test_bulk_copied_links_match(L, recon, lanes):
 
 
 @pytest.mark.parametrize("prec", [stag.STAG_FP16, stag.STAG_FP16 | stag.STAG_HALF_VECTORS])
-def test_bulk_copied_half_links(prec):
+@pytest.mark.parametrize("path", [1, 2])
+def test_tiled_half_links(prec, path):
     """FP16 links (and FP16 Krylov vectors, the gather form of the first kernel)."""
     L = (6, 6, 6, 12)
     V = synth.volume(L)
     U = synth.random_links(L, 0.4, 81)
     b = synth.gaussian_vector(V // 2, 82)
     m = 0.1
-    x1, it1, tr1 = solve_with(L, U, b, m, prec, False, 1, 2)
+    x1, it1, tr1 = solve_with(L, U, b, m, prec, False, path, 2)
     t = oracle.true_residual(L, U, m, b, x1)
     assert t <= 1e-10 and abs(t - tr1) <= 1e-12 + 0.05 * t
