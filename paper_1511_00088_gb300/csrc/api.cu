@@ -427,14 +427,21 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
       l2modes = (a1.nsys == 1 && lb <= 1.25 * (double)c->l2_max_persist) ? 0b10 : 0b01;
     }
   }
+  // STAG_LANES = 1 or 2 fixes the lanes of both kernels; two digits (12, 21
+  // ...) those of the first and the second
   const char *force = getenv("STAG_LANES");
-  const int fl = (force && (force[0] == '1' || force[0] == '2') && force[1] == 0) ? force[0] - '0' : 0;
+  int fl1 = 0, fl2 = 0;
+  if (force && (force[0] == '1' || force[0] == '2')) {
+    if (force[1] == 0) fl1 = fl2 = force[0] - '0';
+    else if ((force[1] == '1' || force[1] == '2') && force[2] == 0) fl1 = force[0] - '0', fl2 = force[1] - '0';
+  }
+  const bool fl = fl1 != 0;
   std::vector<CgForm> cand;
   for (int p = 0; p < 2; ++p)
     for (int t = 0; t < 3; ++t)
       for (int l1 = 1; l1 <= 2; ++l1)
         for (int l2 = 1; l2 <= 2; ++l2)
-          if ((l2modes >> p & 1) && (modes >> t & 1) && (!fl || (l1 == fl && l2 == fl))) {
+          if ((l2modes >> p & 1) && (modes >> t & 1) && (!fl || (l1 == fl1 && l2 == fl2))) {
             CgForm f;
             f.tma = t;
             f.l1 = l1;
