@@ -304,6 +304,15 @@ int links_tile_for(stag_ctx *c, int P, const void **out) {
   return STAG_OK;
 }
 
+// The L2 set-aside for persisting lines, held only while work that marks links
+// persisting runs: set aside and unused, it still cost 16-source solves (which
+// never mark anything persisting) most of their L2 hits.
+void l2_setaside(stag_ctx *c, bool on) {
+  if (!c->l2persist) return;
+  cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, on ? c->l2_max_persist : 0);
+  cudaGetLastError();
+}
+
 // the L2 window of the CG kernels' links for link path tma (DsArgs::tma)
 void set_l2_window(stag_ctx *c, int P, int tma, int on, DsArgs &a) {
   a.l2_base = nullptr;
@@ -487,6 +496,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
     a1.tma = a2.tma = f.tma;
     set_l2_window(c, LP, f.tma, f.l2p, a1);
     set_l2_window(c, LP, f.tma, f.l2p, a2);
+    if (f.l2p) l2_setaside(c, true);
     for (int i = 0; i < 22; ++i) {
       if (i == 2) CK(cudaEventRecord(e0, c->stream));
       CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, f.l1, nb1[q], c->stream, a1));
@@ -498,7 +508,10 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
     CK(cudaEventElapsedTime(&ms, e0, e1));
     tot[q] += ms;
     // each candidate starts without persisting lines
-    if (c->l2persist) cudaCtxResetPersistingL2Cache();
+    if (f.l2p) {
+      cudaCtxResetPersistingL2Cache();
+      l2_setaside(c, false);
+    }
     cudaGetLastError();
   }
   cudaEventDestroy(e0);
@@ -1090,8 +1103,11 @@ int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[])
   CK(cudaStreamSynchronize(c->stream));
   c->last_nsys = nsys;
   // the solve's persisting L2 lines back to normal (the next user of L2, or a
-  // flush between timed solves, may evict them)
-  if (c->l2persist) cudaCtxResetPersistingL2Cache();
+  // flush between timed solves, may evict them) and the set-aside released
+  if (w.l2p) {
+    cudaCtxResetPersistingL2Cache();
+    l2_setaside(c, false);
+  }
   cudaGetLastError();
   if (hf[4] != 0) {
     c->err = "a CG kernel gave up waiting for its bulk-copied links; the solution is void";
@@ -1125,11 +1141,15 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
       }
     }
     if (w.exec) {
+      if (w.l2p) l2_setaside(c, true);
       CK(cudaGraphLaunch(w.exec, c->stream));
       ran = true;
     }
   }
-  if (!ran) CKS(solve_eager(c, maxiter));
+  if (!ran) {
+    if (w.l2p) l2_setaside(c, true);
+    CKS(solve_eager(c, maxiter));
+  }
   return solve_finish(c, x, iters, true_res);
 }
 
@@ -1283,12 +1303,17 @@ int ragged_impl(const stag_solve_desc *d, int n, double tol, int maxiter, int pr
     }
     if (exec) {
       stag_ctx *c = c0;
+      for (int i = 0; i < n; ++i)
+        if (d[i].ctx->w.l2p) l2_setaside(d[i].ctx, true);
       CK(cudaGraphLaunch(exec, c0->stream));
       ran = true;
     }
   }
   if (!ran)
-    for (int i = 0; i < n; ++i) CKS(solve_eager(d[i].ctx, maxiter));
+    for (int i = 0; i < n; ++i) {
+      if (d[i].ctx->w.l2p) l2_setaside(d[i].ctx, true);
+      CKS(solve_eager(d[i].ctx, maxiter));
+    }
   int status = STAG_OK;
   for (int i = 0; i < n; ++i) {
     const int st = solve_finish(d[i].ctx, d[i].x, d[i].iters, d[i].true_res);
@@ -1403,12 +1428,6 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
       maxp = maxw = 0;
     cudaGetLastError();
     if (c->l2persist && maxp > 0 && maxw > 0) {
-      // the context's set-aside for persisting lines (released with the context)
-      size_t cur = 0;
-      if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur < (size_t)maxp &&
-          cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) != cudaSuccess)
-        maxp = 0;
-      cudaGetLastError();
       c->l2_max_persist = (size_t)maxp;
       c->l2_max_window = (size_t)maxw;
     }
@@ -1663,6 +1682,7 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
         launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, c->stream, a2) != cudaSuccess)
       st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
   }
+  if (w.l2p) l2_setaside(c, true);
   if (st == STAG_OK && cudaEventRecord(ev[0], c->stream) != cudaSuccess)
     st = fail(c, STAG_ERR_CUDA, "cudaEventRecord", cudaGetLastError());
   for (int i = 0; i < nlaunch && st == STAG_OK; ++i) {
@@ -1683,7 +1703,10 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   }
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
-  if (c->l2persist) cudaCtxResetPersistingL2Cache();
+  if (w.l2p) {
+    cudaCtxResetPersistingL2Cache();
+    l2_setaside(c, false);
+  }
   cudaGetLastError();
   if (st != STAG_OK) return st;
   *ms_per_launch = tot / nlaunch;
