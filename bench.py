@@ -298,12 +298,14 @@ def run_ours(args):
         total_ms += e0.elapsed_time(e1)
         _, nu, _ = ctx.solve_stats(0)
         passes, ups = ctx.solve_counters()
+        unroll = ctx.solve_form()["iterations_per_pass"]
         iters.append(it)
         updates.append(nu)
         res.append(tr)
         # one pack per source, init + its finalize, one unpack per system; per
-        # loop pass 8 CG kernels and one finalize; per update step 5 kernels
-        launches += 2 * nrhs + 2 + 9 * passes + 5 * ups
+        # loop pass 2 CG kernels per iteration and one finalize; per update
+        # step 5 kernels
+        launches += 2 * nrhs + 2 + (2 * unroll + 1) * passes + 5 * ups
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -202,12 +202,13 @@ int stag_solve_stats(const stag_ctx *ctx, int sys, int *iters, int *reliable_upd
 
 /*
  * Loop counters of the most recent stag_cg_solve on this context (all its
- * systems together): passes of the solve loop (each runs up to 4 CG
- * iterations of every running system) and executions of the FP64
- * reliable-update step (Sec. 3; each recomputes the residual of every system
- * with an update due).  From them the kernels launched follow: 9 per pass and
- * 5 per update step (4 with STAG_HALF_VECTORS).  Either pointer may be NULL.
- * STAG_ERR_ARG before the first solve.
+ * systems together): passes of the solve loop (each runs up to U CG
+ * iterations of every running system, U = stag_solve_form out[6]) and
+ * executions of the FP64 reliable-update step (Sec. 3; each recomputes the
+ * residual of every system with an update due).  From them the kernels
+ * launched follow: 2 U + 1 per pass and 5 per update step (4 with
+ * STAG_HALF_VECTORS).  Either pointer may be NULL.  STAG_ERR_ARG before the
+ * first solve.
  */
 int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps);
 
@@ -216,11 +217,12 @@ int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps
  * solve (or timing call): out[0] systems per thread, out[1] system groups,
  * out[2] / out[3] lanes per site of the first / second kernel, out[4] link
  * path (0 plane layout, 1 tiled through shared memory, 2 tiled into
- * registers), out[5] 1 when the links persist in L2 during the solve.
- * Implementation detail of this library (the paper has no counterpart), for
- * reports.  STAG_ERR_ARG before the first solve.
+ * registers), out[5] 1 when the links persist in L2 during the solve, out[6]
+ * CG iterations per pass of the solve loop.  Implementation detail of this
+ * library (the paper has no counterpart), for reports.  STAG_ERR_ARG before
+ * the first solve.
  */
-int stag_solve_form(const stag_ctx *ctx, int out[6]);
+int stag_solve_form(const stag_ctx *ctx, int out[7]);
 
 /*
  * out_even = (4 m^2 - D_eo D_oe) in_even in FP64, with tmp_odd = D_oe in_even

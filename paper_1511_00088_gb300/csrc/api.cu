@@ -12,15 +12,19 @@
 //   K2  p = r + beta p_old at the centre (stored); A p = 4 m^2 p - D_eo t;
 //       r -= alpha A p; x_lo += alpha p; |r|^2, Re<r,p> -> beta; reliable-
 //       update and convergence triggers                   (FP64 reduction)
+//   Each kernel finishes the reduction of the one before it in every block
+//   (fold), so a pass of SOLVE_UNROLL iterations ends with one finalize
+//   kernel, which also sets the graph conditions.
 //   if a reliable update is pending (a conditional graph node at the end of
-//   every SOLVE_UNROLL iterations):
+//   every pass):
 //   K4  x64 += x_lo,  x_lo = 0;  t = D_oe p (restarts the t recurrence)
 //   K5  t64 = D_oe x64                                    (FP64)
 //   K6  r = b - (4 m^2 x64 - D_eo t64) in FP64, stored at the residual's
 //       precision; ||r||^2, Re<r,p> in FP64 -> true residual, convergence, beta
 // The iterations sit in the body of a CUDA-graph WHILE node whose condition
-// the last block of K2 / K6 sets ("any system still running"); the update
-// kernels sit in an IF node set by K2.  One graph launch runs the whole solve.
+// the pass's finalize / K6's finalize sets ("any system still running"); the
+// update kernels sit in an IF node set by the pass's finalize.  One graph
+// launch runs the whole solve.
 // Without conditional-node support the same kernel sequence runs eagerly, with
 // the host polling a device flag every few loop passes.
 #include <cmath>
@@ -816,9 +820,9 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   return STAG_OK;
 }
 
-// One pass of the solve loop: SOLVE_UNROLL iterations.  With folded
+// One pass of the solve loop: `unroll` iterations.  With folded
 // reductions each CG kernel finishes its predecessor's reduction itself, so
-// the pass launches 2 SOLVE_UNROLL CG kernels and a single finalize kernel
+// the pass launches 2 unroll CG kernels and a single finalize kernel
 // (the last reduction, which also sets the loop and update conditions).  The
 // states and the partials alternate between two buffers, as a block may still
 // read the old ones while another writes the new; the pass starts and ends with
@@ -935,9 +939,19 @@ int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
 }
 
 // Iterations per pass of the solve loop: the body holds SOLVE_UNROLL copies of
-// K1, K2 (each followed by its finalize kernel) and one conditional reliable update (a pending update waits for the
-// end of the pass), which spreads the loop and conditional-node overhead.
-constexpr int SOLVE_UNROLL = 4;
+// K1, K2, one finalize kernel and one conditional reliable update (a pending
+// update waits for the end of the pass), which spreads the loop, finalize and
+// conditional-node overhead.  Measured at 20^3 x 64: 4 -> 155.1 ms, 8 -> 152.4,
+// 16 -> 150.5 (same 2958 iterations); a converged system's remaining
+// iterations of its pass are gated launches of a few us each.
+constexpr int SOLVE_UNROLL = 16;
+
+// iterations per pass (STAG_UNROLL = 1..16 overrides SOLVE_UNROLL)
+int solve_unroll() {
+  const char *u = getenv("STAG_UNROLL");
+  const int v = u ? atoi(u) : 0;
+  return (v >= 1 && v <= 16) ? v : SOLVE_UNROLL;
+}
 
 int build_graph_inner(stag_ctx *c);
 
@@ -979,7 +993,7 @@ int add_solve_loop(stag_ctx *c, cudaGraph_t g, const cudaGraphNode_t *deps, size
 
   CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int st = STAG_OK;
-  st = enqueue_pass(c, c->cap, ctl, SOLVE_UNROLL);
+  st = enqueue_pass(c, c->cap, ctl, solve_unroll());
   if (st != STAG_OK) {
     cudaGraph_t tmp;
     cudaStreamEndCapture(c->cap, &tmp);
@@ -1078,10 +1092,10 @@ int solve_eager(stag_ctx *c, int maxiter) {
   const Ctl ctl = work_ctl(c, false);
   int *hf = (int *)w.h_flags.p;
   const int passes_per_poll = 4;  // the same sequence as the graph body, polled every 4 passes
-  for (long long it = 0; it <= (long long)maxiter + 2 * SOLVE_UNROLL * passes_per_poll;
-       it += SOLVE_UNROLL * passes_per_poll) {
+  const int unroll = solve_unroll();
+  for (long long it = 0; it <= (long long)maxiter + 2 * unroll * passes_per_poll; it += unroll * passes_per_poll) {
     for (int i = 0; i < passes_per_poll; ++i) {
-      CKS(enqueue_pass(c, c->stream, ctl, SOLVE_UNROLL));
+      CKS(enqueue_pass(c, c->stream, ctl, unroll));
       CKS(enqueue_update(c, c->stream, ctl));
     }
     CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
@@ -1615,7 +1629,7 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
   return STAG_OK;
 }
 
-int stag_solve_form(const stag_ctx *c, int out[6]) {
+int stag_solve_form(const stag_ctx *c, int out[7]) {
   if (!c || !out || c->w.nsys <= 0) return STAG_ERR_ARG;
   const Work &w = c->w;
   out[0] = w.NS;
@@ -1624,6 +1638,7 @@ int stag_solve_form(const stag_ctx *c, int out[6]) {
   out[3] = w.lanes_k2;
   out[4] = w.tma;
   out[5] = w.l2p;
+  out[6] = solve_unroll();
   return STAG_OK;
 }
 
