@@ -687,8 +687,11 @@ __global__ void k_finalize(const Ctl c, int fin, int nbx, int nv, int nsys, cons
 //  2: the tiled site-owned copy loaded straight into registers: a warp's 8
 //     links then lie in one contiguous block of 32 LT-site rows (fewer DRAM
 //     pages per load round than 48 planes of the plane layout).
+#ifndef STAG_DS_MINB
+#define STAG_DS_MINB 1  // minimum resident blocks per SM asked of ptxas (reduced-precision links)
+#endif
 template <int LP, int RECON, int VP, int OP, int NS, int EPI, int BT, int LANES, int TMA = 0>
-__global__ void __launch_bounds__(BT, LP == P64 ? 4 : 1) k_dslash(const DsArgs a) {
+__global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(const DsArgs a) {
   static_assert(!TMA || (NS == 1 && LP != P64), "tiled links: one system, reduced-precision links");
   typedef typename Tr<LP>::R R;
   typedef typename Tr<LP>::S2 LS2;
