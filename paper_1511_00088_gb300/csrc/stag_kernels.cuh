@@ -468,10 +468,12 @@ __device__ __forceinline__ bool sys_gate(const Ctl &c, int gate, int j, int nsys
 //                alpha = rho / (4 m^2 |p|^2 + |t|^2)  (= <p, A p>, D_eo^dag = -D_oe)
 //   FIN_ALPHA_R: as FIN_ALPHA with |p|^2 = rho + 2 beta Re<r, p_old> + beta^2 |p_old|^2
 //                (the first kernel then only reduces |t|^2)
-//   FIN_NORM:    sums |r|^2, Re<r, p>: beta = rho_new / rho; a reliable update
-//                becomes pending when |r| < delta r_max; when |r| <= tol |b| or
-//                the iteration cap is reached the system stops (done = 3) until
-//                the pending FP64 recomputation decides
+//   FIN_NORM:    sums |r|^2, Re<r, p>: beta = rho_new / rho; when |r| < delta
+//                r_max (reliable update), |r| <= tol |b| or the iteration cap is
+//                reached, an update becomes pending and the system pauses
+//                (done = 3) until the FP64 recomputation decides: iterating on
+//                past the trigger (up to a pass of 16 iterations) let the FP32
+//                recurrences run below their rounding floor on small systems
 //   FIN_RESID:   sums of the FP64 recomputation |b - A x|^2, Re<r, p>: converged,
 //                capped, or continue with rho = |r_true|^2, beta = rho / rho_prev
 //   FIN_INIT:    |b|^2 and |r|^2 of the starting residual
@@ -498,11 +500,12 @@ __device__ __forceinline__ void finalize_system(SysState &s, int fin, const doub
     s.rho_prev = s.rho;
     s.beta = rr / s.rho;
     s.rho = rr;
-    if (rr <= s.tol * s.tol * s.bnorm2 || s.iter >= s.maxiter) {
+    // convergence candidate, iteration cap or reliable-update trigger: the
+    // system pauses (done = 3, its kernels gated off) until the update step at
+    // the end of the pass recomputes its residual in FP64 and decides
+    if (rr <= s.tol * s.tol * s.bnorm2 || s.iter >= s.maxiter || rr < s.delta * s.delta * s.rmax2) {
       s.update = 1;
       s.done = 3;
-    } else if (rr < s.delta * s.delta * s.rmax2) {
-      s.update = 1;
     }
   } else if (fin == FIN_RESID) {
     const double rr = sum[0];
