@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--links", default="recon12", choices=["full", "recon12"],
                     help="storage of the reduced-precision links (the FP64 copy is always full)")
+    ap.add_argument("--masses", default=None,
+                    help="comma-separated masses solved together with every source (overrides --mass; "
+                         "the 12-source x 4-mass workload: --nrhs 12 --masses 0.01,0.02,0.03,0.05)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="sources solved together in one call (the 48^3x96 workload uses 16)")
     ap.add_argument("--seed-config", type=int, default=1,
@@ -80,12 +83,16 @@ def link_mb(L, prec, links):
     return 4 * math.prod(L) * (6 if links == "recon12" else 9) * cb / 1e6
 
 
+def mass_str(mass):
+    return ",".join(f"{m:g}" for m in mass) if isinstance(mass, (list, tuple)) else f"{mass:g}"
+
+
 def workload_config(L, mass, tol, prec, links="full", nrhs=1):
     return {
         "link_storage": ("reconstruct-12 (rows 0, 1 stored; row 2 = conj(row0 x row1) in registers)"
                          if links == "recon12" else "full 3x3") + f" at {prec.upper()}; FP64 copy full",
         "workload": f"{L[0]}^3x{L[3]} even-odd staggered CG, {prec.upper()} inner iteration, "
-                    f"FP64 reliable updates (delta=0.1), m={mass}, {nrhs} RHS, true residual {tol:g}"
+                    f"FP64 reliable updates (delta=0.1), m={mass_str(mass)}, {nrhs} RHS, true residual {tol:g}"
         if L[0] == L[1] == L[2] else f"{L} staggered CG",
         "lattice": list(L),
         "links": "reunitarised exp(0.4 i H), synthetic (stands in for the MILC 20^3x64 ensemble)",
@@ -261,18 +268,20 @@ def run_ours(args):
         U = synth.random_links(L, 0.4, synth.seed_for(cfg, 1))
         Ud = torch.from_numpy(U).cuda()
     nrhs = args.nrhs
+    masses = [float(m) for m in args.masses.split(",")] if args.masses else [args.mass]
+    nsys = nrhs * len(masses)
     bs = [synth.gaussian_vector(Ve, synth.seed_for(cfg, 2 + rank * nrhs + r)) for r in range(nrhs)]
     b = bs[0]
     stream = torch.cuda.current_stream()
     ctx = stag.Context(L, recon12=(args.links == "recon12"), stream=stream.cuda_stream)
     ctx.links_upload(Ud)
     bds = [torch.from_numpy(v).cuda() for v in bs]
-    xds = [torch.empty_like(v) for v in bds]
+    xds = [torch.empty_like(bds[0]) for _ in range(nsys)]
     bd, xd = bds[0], xds[0]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def solve():
-        xs, st, it, tr = ctx.cg_solve(bds, [args.mass], tol=args.tol, maxiter=50000,
+        xs, st, it, tr = ctx.cg_solve(bds, masses, tol=args.tol, maxiter=50000,
                                       precision=prec, xs=xds)
         return [int(v) for v in it], float(max(tr))
 
@@ -302,10 +311,10 @@ def run_ours(args):
         iters.append(it)
         updates.append(nu)
         res.append(tr)
-        # one pack per source, init + its finalize, one unpack per system; per
-        # loop pass 2 CG kernels per iteration and one finalize; per update
-        # step 5 kernels
-        launches += 2 * nrhs + 2 + (2 * unroll + 1) * passes + 5 * ups
+        # one pack per source and mass, init + its finalize, one unpack per
+        # system; per loop pass 2 CG kernels per iteration and one finalize;
+        # per update step 5 kernels
+        launches += 2 * nsys + 2 + (2 * unroll + 1) * passes + 5 * ups
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -327,13 +336,13 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     bhs = [torch.from_numpy(v).pin_memory() for v in bs]
-    xhs = [torch.empty_like(v).pin_memory() for v in bhs]
+    xhs = [torch.empty_like(bhs[0]).pin_memory() for _ in range(nsys)]
     e2e_ms, e2e_it = [], []
     for k in range(0 if args.no_extras else max(1, min(args.steps, 5))):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t = time.perf_counter()
-        xs, st, it, tr = ctx.cg_solve(bhs, [args.mass], tol=args.tol, maxiter=50000,
+        xs, st, it, tr = ctx.cg_solve(bhs, masses, tol=args.tol, maxiter=50000,
                                       precision=prec, xs=xhs)
         e2e_ms.append(1e3 * (time.perf_counter() - t))
         e2e_it.append(int(sum(it)))
@@ -374,13 +383,13 @@ def run_ours(args):
         # several sources: the FP64 and FP32 single-source references only)
         cmp = ((("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16),
                 ("fp32", stag.STAG_FP32), ("fp16_half_vectors", stag.STAG_FP16 | stag.STAG_HALF_VECTORS))
-               if nrhs == 1 else (("fp64", stag.STAG_FP64), ("fp32", stag.STAG_FP32)))
+               if nsys == 1 else (("fp64", stag.STAG_FP64), ("fp32", stag.STAG_FP32)))
         for name, p in cmp:
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            xs, st, it, tr = ctx.cg_solve([bd], [args.mass], tol=args.tol, maxiter=30000, precision=p,
+            xs, st, it, tr = ctx.cg_solve([bd], masses[:1], tol=args.tol, maxiter=30000, precision=p,
                                           xs=[xd], allow_not_converged=True)
             e1.record(stream)
             e1.synchronize()
@@ -389,18 +398,18 @@ def run_ours(args):
                                     "reliable_updates": nu, "true_res": float(tr[0]),
                                     "status": stag.status_name(st)}
         for name, p in ((("fp64", stag.STAG_FP64), ("fp16", stag.STAG_FP16), ("bf16", stag.STAG_BF16))
-                        if nrhs == 1 else ()):
+                        if nsys == 1 else ()):
             m, by = ctx.time_dslash(p, nlaunch=50)
             extras[f"dslash_{name}"] = {"ms": m, "GB/s": by / (m * 1e-3) / 1e9,
                                         "GFLOP/s": DSLASH_FLOP_PER_SITE * Ve / (m * 1e-3) / 1e9}
         # FP64 single-source time over the timed solve's time per source
-        extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps / nrhs)
+        extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps / nsys)
 
     cpu = None
     if ws == 1 and rank == 0 and not args.no_extras:
         if U is None:
             U = Ud.cpu().numpy()
-        g, it, dt = cpu_oracle_sample(L, U, b, args.mass, 12.0)
+        g, it, dt = cpu_oracle_sample(L, U, b, masses[0], 12.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"{it} FP64 CG iterations of the CPU oracle on the same {L} field "
                          f"({dt:.1f} s, single thread)"}
@@ -412,12 +421,12 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": value / PAPER_TX_CG_GFLOPS,
             "dtype": "f32" if args.precision == "fp32" else args.precision.replace("fp", "f"),
             "data": "synthetic",
-            "config": workload_config(L, args.mass, args.tol, args.precision, args.links, nrhs),
-            "time_to_solution_ms": ms_step, "iters": iters[-1] if nrhs > 1 else iters[-1][0],
+            "config": workload_config(L, masses, args.tol, args.precision, args.links, nrhs),
+            "time_to_solution_ms": ms_step, "iters": iters[-1] if nsys > 1 else iters[-1][0],
             "reliable_updates": updates[-1],
             "true_res": max(res),
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 48 * Ve * nrhs,
-                    "d2h_bytes_per_step": 48 * Ve * nrhs, "ms_per_step": e2e_ms_step},
+                    "d2h_bytes_per_step": 48 * Ve * nsys, "ms_per_step": e2e_ms_step},
             "gpu_launches": launches,
             "launch_form": form,
             "roofline": roof,
