@@ -406,6 +406,64 @@ __device__ __forceinline__ void mvdag_acc(const R (&u)[18], const R (&v)[6], R s
   }
 }
 
+#ifndef STAG_FFMA2
+#define STAG_FFMA2 0
+#endif
+#if STAG_FFMA2
+// FP32 forms on Blackwell's packed FP32x2 FMA (two lanes of a float2 per
+// instruction): with v_b = (re, im), a complex multiply-accumulate is
+//   h += Re(U) (v_re, v_im) + Im(U) (-v_im, v_re)       (U v)
+//   h += Re(U) (v_re, v_im) + Im(U) ( v_im, -v_re)      (U^dag v)
+// two packed FMAs instead of four scalar ones; the swizzled v is formed once
+// per colour and reused by the three rows.  Off by default (-DSTAG_FFMA2=1):
+// the swizzled copies raise the CG kernels from 117-126 to 126-136 registers,
+// past the 128 that keep 4 blocks per SM -- single-source solves gained 1.3 %,
+// 16-source solves lost 13 %.
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ void mv_acc(const float (&u)[18], const float (&v)[6], float sgn, float (&acc)[6]) {
+  float2 vs[3], vw[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    vs[b] = make_float2(v[2 * b], v[2 * b + 1]);
+    vw[b] = make_float2(-v[2 * b + 1], v[2 * b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      h = __ffma2_rn(bcast2(u[2 * (3 * a + b)]), vs[b], h);
+      h = __ffma2_rn(bcast2(u[2 * (3 * a + b) + 1]), vw[b], h);
+    }
+    const float2 r = __ffma2_rn(bcast2(sgn), h, make_float2(acc[2 * a], acc[2 * a + 1]));
+    acc[2 * a] = r.x;
+    acc[2 * a + 1] = r.y;
+  }
+}
+
+__device__ __forceinline__ void mvdag_acc(const float (&u)[18], const float (&v)[6], float sgn, float (&acc)[6]) {
+  float2 vs[3], vd[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    vs[b] = make_float2(v[2 * b], v[2 * b + 1]);
+    vd[b] = make_float2(v[2 * b + 1], -v[2 * b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      h = __ffma2_rn(bcast2(u[2 * (3 * b + a)]), vs[b], h);
+      h = __ffma2_rn(bcast2(u[2 * (3 * b + a) + 1]), vd[b], h);
+    }
+    const float2 r = __ffma2_rn(bcast2(sgn), h, make_float2(acc[2 * a], acc[2 * a + 1]));
+    acc[2 * a] = r.x;
+    acc[2 * a + 1] = r.y;
+  }
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // geometry
 // ---------------------------------------------------------------------------
