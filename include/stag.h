@@ -218,11 +218,13 @@ int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps
  * out[2] / out[3] lanes per site of the first / second kernel, out[4] link
  * path (0 plane layout, 1 tiled through shared memory, 2 tiled into
  * registers), out[5] 1 when the links persist in L2 during the solve, out[6]
- * CG iterations per pass of the solve loop.  Implementation detail of this
- * library (the paper has no counterpart), for reports.  STAG_ERR_ARG before
- * the first solve.
+ * CG iterations per pass of the solve loop, out[7] 1 when the CG kernels
+ * share each chunk's links in shared memory among the out[0] systems of a
+ * block (one warp per system).  Implementation detail of this library (the
+ * paper has no counterpart), for reports.  STAG_ERR_ARG before the first
+ * solve.
  */
-int stag_solve_form(const stag_ctx *ctx, int out[7]);
+int stag_solve_form(const stag_ctx *ctx, int out[8]);
 
 /*
  * out_even = (4 m^2 - D_eo D_oe) in_even in FP64, with tmp_odd = D_oe in_even

@@ -127,6 +127,7 @@ struct Work {
   int nbx_k1 = 0, nbx_k2 = 0;      // blocks per system group of the two CG kernels
   int tma = 0;                     // link path of the CG kernels (DsArgs::tma)
   int l2p = 0;                     // their links persist in L2 during a solve
+  int mrhs = 0;                    // > 0: the CG kernels are k_dslash_mrhs with mrhs systems per block
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
@@ -416,6 +417,55 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
 // alternates the two kernels, each starting on the cache state the other
 // leaves.  Cached as 1000 l2p + 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2
 // fixes the lanes.
+// Blocks per system group of k_dslash_mrhs with nsw systems per block: one
+// wave of resident blocks, at most one per 32-site chunk.
+int mrhs_blocks(stag_ctx *c, int recon, int nsw, int EPI, int G, int *nbx) {
+  const int full = (c->Ve + 31) / 32;
+  *nbx = full;
+  if (!c->persist) return STAG_OK;
+  DsArgs none;
+  memset(&none, 0, sizeof none);
+  const void *k = nullptr;
+  CK(launch_dslash_mrhs(P32, recon, nsw, EPI, 0, c->stream, none, &k));
+  int per_sm = 0, nsm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * nsw, 0));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  int n = per_sm * nsm / G;
+  if (n < 1) n = 1;
+  if (n < full) *nbx = n;
+  return STAG_OK;
+}
+
+// total time of 2 x 20 alternating launch pairs of the two k_dslash_mrhs CG
+// kernels with nsw systems per block (the measure tune_cg_pair reports)
+int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float *ms_out) {
+  const int G = (a1.nsys + nsw - 1) / nsw;
+  a1.ngroups = a2.ngroups = G;
+  int n1 = 0, n2 = 0;
+  CKS(mrhs_blocks(c, recon, nsw, EPI_CG_K1R, G, &n1));
+  CKS(mrhs_blocks(c, recon, nsw, EPI_CG_K2, G, &n2));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float tot = 0.f;
+  for (int o = 0; o < 2; ++o) {
+    for (int i = 0; i < 22; ++i) {
+      if (i == 2) CK(cudaEventRecord(e0, c->stream));
+      CK(launch_dslash_mrhs(P32, recon, nsw, EPI_CG_K1R, n1 * G, c->stream, a1));
+      CK(launch_dslash_mrhs(P32, recon, nsw, EPI_CG_K2, n2 * G, c->stream, a2));
+    }
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    tot += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = tot;
+  return STAG_OK;
+}
+
 struct CgForm {
   int tma = 0, l1 = 1, l2 = 1, l2p = 0;  // link path, lanes of the two kernels, L2-persisting links
 };
@@ -617,7 +667,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
   w.NS64 = nsys >= 4 ? 4 : 1;
   w.G64 = (nsys + w.NS64 - 1) / w.NS64;
   const int Ve = c->Ve;
-  const int nbx_ds_max = ds_blocks(Ve, 2);
+  const int nbx_ds_max = (Ve + 31) / 32;  // most blocks per group of any CG kernel (32-site chunks)
   w.nbx_bl = (Ve + BLAS_BT - 1) / BLAS_BT;
   w.pstride = nbx_ds_max > w.nbx_bl ? nbx_ds_max : w.nbx_bl;
   CK(w.b64.ensure(P64, nsys, Ve));
@@ -685,6 +735,15 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
       const int f = fns[0] - '0';
       if (f <= nsys && !(f == 8 && prec == P64)) cands.assign(1, f);
     }
+    // the shared-memory kernels (k_dslash_mrhs): FP32 links and vectors, 4 or 8
+    // systems per block; encoded as 100 + nsw among the candidates
+    if (prec == P32 && VP == P32 && !(fns && fns[0] != 0)) {
+      if (nsys >= 4) cands.push_back(104);
+      if (nsys >= 8) cands.push_back(108);
+    }
+    const char *fmr = getenv("STAG_MRHS");
+    if (fmr && (fmr[0] == '4' || fmr[0] == '8') && fmr[1] == 0 && prec == P32 && VP == P32 && nsys >= 2)
+      cands.assign(1, 100 + (fmr[0] - '0'));
     int best_ns = cands[0];
     if (cands.size() > 1) {
       const TuneKey nkey(prec, recon, VP, 2000 + nsys, tma_ok ? 1 : 0, c->dims[0], c->dims[1], c->dims[2],
@@ -702,10 +761,14 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
       if (!cached) {
         float best_ms = 1e30f;
         for (int ns : cands) {
-          a.ngroups = a2.ngroups = (nsys + ns - 1) / ns;
-          CgForm f;
           float ms = -1.f;
-          CKS(tune_cg_pair(c, prec, recon, VP, ns, epi1, a, a2, tma_ok && ns == 1, &f, &ms));
+          if (ns > 100) {
+            CKS(time_mrhs_pair(c, recon, ns - 100, a, a2, &ms));
+          } else {
+            a.ngroups = a2.ngroups = (nsys + ns - 1) / ns;
+            CgForm f;
+            CKS(tune_cg_pair(c, prec, recon, VP, ns, epi1, a, a2, tma_ok && ns == 1, &f, &ms));
+          }
           if (ms >= 0.f && ms < best_ms) {
             best_ms = ms;
             best_ns = ns;
@@ -716,17 +779,26 @@ int work_prepare(stag_ctx *c, int nsys, int precision) {
         tune_cache_store(nkey, best_ns);
       }
     }
-    w.NS = best_ns;
+    w.mrhs = best_ns > 100 ? best_ns - 100 : 0;
+    w.NS = w.mrhs ? w.mrhs : best_ns;
     w.G = (nsys + w.NS - 1) / w.NS;
     a.ngroups = a2.ngroups = w.G;
-    CgForm form;
-    CKS(tune_cg_pair(c, prec, recon, VP, w.NS, epi1, a, a2, tma_ok && w.NS == 1, &form));
-    w.tma = form.tma;
-    w.lanes_k1 = form.l1;
-    w.lanes_k2 = form.l2;
-    w.l2p = form.l2p;
-    CKS(cg_blocks(c, prec, recon, VP, w.NS, epi1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
-    CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, w.tma, &w.nbx_k2));
+    if (w.mrhs) {
+      w.tma = 0;
+      w.lanes_k1 = w.lanes_k2 = 1;
+      w.l2p = 0;
+      CKS(mrhs_blocks(c, recon, w.mrhs, EPI_CG_K1R, w.G, &w.nbx_k1));
+      CKS(mrhs_blocks(c, recon, w.mrhs, EPI_CG_K2, w.G, &w.nbx_k2));
+    } else {
+      CgForm form;
+      CKS(tune_cg_pair(c, prec, recon, VP, w.NS, epi1, a, a2, tma_ok && w.NS == 1, &form));
+      w.tma = form.tma;
+      w.lanes_k1 = form.l1;
+      w.lanes_k2 = form.l2;
+      w.l2p = form.l2p;
+      CKS(cg_blocks(c, prec, recon, VP, w.NS, epi1, w.lanes_k1, w.G, w.tma, &w.nbx_k1));
+      CKS(cg_blocks(c, prec, recon, VP, w.NS, EPI_CG_K2, w.lanes_k2, w.G, w.tma, &w.nbx_k2));
+    }
   }
   // the thread mapping of the plain inner and the FP64 half operators
   CKS(tune_lanes(c, prec, recon, VP, w.NS, w.G, nsys, lo, w.p.arg(), w.t.arg(), &w.lanes));
@@ -773,6 +845,15 @@ BlasArgs blas_base(stag_ctx *c, const Ctl &ctl) {
   return b;
 }
 
+// One of the two CG kernels (kernel 0: epi1 = EPI_CG_K1R or EPI_CG_K1;
+// kernel 1: EPI_CG_K2) in the workspace's tuned launch form.
+cudaError_t launch_cg(stag_ctx *c, int kernel, int epi, cudaStream_t s, const DsArgs &a) {
+  Work &w = c->w;
+  const int nb = (kernel == 0 ? w.nbx_k1 : w.nbx_k2) * w.G;
+  if (w.mrhs) return launch_dslash_mrhs(w.prec, w.recon, w.mrhs, epi, nb, s, a);
+  return launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi, kernel == 0 ? w.lanes_k1 : w.lanes_k2, nb, s, a);
+}
+
 // K1..K3
 int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   Work &w = c->w;
@@ -801,12 +882,12 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
     // t = D_oe r + beta t_old: one gathered vector; |p|^2 from the scalar recurrence
     a.out = w.t.arg();
     a.fin = FIN_ALPHA_R;
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1R, w.lanes_k1, nbx * w.G, s, a));
+    CK(launch_cg(c, 0, EPI_CG_K1R, s, a));
     CK(launch_finalize(ctl, FIN_ALPHA_R, nbx, 1, w.nsys, s, c->pdl));
   } else {
     // FP16/BF16 Krylov vectors: no t recurrence (its rounding would accumulate)
     a.fin = FIN_ALPHA;
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K1, w.lanes_k1, nbx * w.G, s, a));
+    CK(launch_cg(c, 0, EPI_CG_K1, s, a));
     CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s, c->pdl));
   }
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
@@ -815,7 +896,7 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.center = w.p.arg();
   a.fin = FIN_NORM;
   const int nbx2 = w.nbx_k2;
-  CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, nbx2 * w.G, s, a));
+  CK(launch_cg(c, 1, EPI_CG_K2, s, a));
   CK(launch_finalize(ctl, FIN_NORM, nbx2, 2, w.nsys, s, c->pdl));
   return STAG_OK;
 }
@@ -867,8 +948,7 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
     a.fold_nbx = w.nbx_k2;
     a.fold_nv = 2;
     a.st_out = S[1 - cur];
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, rec ? EPI_CG_K1R : EPI_CG_K1, w.lanes_k1, w.nbx_k1 * w.G,
-                     s, a));
+    CK(launch_cg(c, 0, rec ? EPI_CG_K1R : EPI_CG_K1, s, a));
     if (u > 0) cur = 1 - cur;
     // K2: p = r + beta p_old; r -= alpha (4 m^2 p - D_eo t); x += alpha p; folds K1's sums
     a.par_out = 0;
@@ -882,7 +962,7 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
     a.fold_nbx = w.nbx_k1;
     a.fold_nv = rec ? 1 : 2;
     a.st_out = S[1 - cur];
-    CK(launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, s, a));
+    CK(launch_cg(c, 1, EPI_CG_K2, s, a));
     cur = 1 - cur;
   }
   Ctl f = ctl;
@@ -1629,7 +1709,7 @@ int stag_solve_stats(const stag_ctx *c, int sys, int *iters, int *reliable_updat
   return STAG_OK;
 }
 
-int stag_solve_form(const stag_ctx *c, int out[7]) {
+int stag_solve_form(const stag_ctx *c, int out[8]) {
   if (!c || !out || c->w.nsys <= 0) return STAG_ERR_ARG;
   const Work &w = c->w;
   out[0] = w.NS;
@@ -1639,6 +1719,7 @@ int stag_solve_form(const stag_ctx *c, int out[7]) {
   out[4] = w.tma;
   out[5] = w.l2p;
   out[6] = solve_unroll();
+  out[7] = w.mrhs ? 1 : 0;
   return STAG_OK;
 }
 
@@ -1693,17 +1774,16 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   for (auto &e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) st = fail(c, STAG_ERR_CUDA, "cudaEventCreate", cudaGetLastError());
   for (int i = 0; i < 2 && st == STAG_OK; ++i) {  // warm-up pair
-    if (launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi1, w.lanes_k1, w.nbx_k1 * w.G, c->stream, a1) != cudaSuccess ||
-        launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, c->stream, a2) != cudaSuccess)
+    if (launch_cg(c, 0, epi1, c->stream, a1) != cudaSuccess || launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess)
       st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
   }
   if (w.l2p) l2_setaside(c, true);
   if (st == STAG_OK && cudaEventRecord(ev[0], c->stream) != cudaSuccess)
     st = fail(c, STAG_ERR_CUDA, "cudaEventRecord", cudaGetLastError());
   for (int i = 0; i < nlaunch && st == STAG_OK; ++i) {
-    if (launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi1, w.lanes_k1, w.nbx_k1 * w.G, c->stream, a1) != cudaSuccess ||
+    if (launch_cg(c, 0, epi1, c->stream, a1) != cudaSuccess ||
         cudaEventRecord(ev[2 * i + 1], c->stream) != cudaSuccess ||
-        launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, EPI_CG_K2, w.lanes_k2, w.nbx_k2 * w.G, c->stream, a2) != cudaSuccess ||
+        launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess ||
         cudaEventRecord(ev[2 * i + 2], c->stream) != cudaSuccess)
       st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
   }

@@ -84,6 +84,11 @@ cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int la
 cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a, const void **kptr);
 
+// k_dslash_mrhs<LP, recon, nsw, EPI> (LP = P32; nsw = 4 or 8 systems per block
+// of 32 nsw threads; EPI_CG_K1R or EPI_CG_K2) on nblocks blocks; kptr as above
+cudaError_t launch_dslash_mrhs(int LP, int recon, int nsw, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
+                               const void **kptr = nullptr);
+
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 // k_finalize over the partials of the kernel just launched: nbx blocks per
 // system group, nv values per system (pdl: launched as a programmatic

@@ -494,6 +494,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialisation may be scheduled while its predecessor in the stream is still
@@ -1120,6 +1125,153 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
 
   if (EPI == EPI_CG_K1 || EPI == EPI_CG_K1R || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
     if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the two CG kernels for several systems, the links shared in shared memory
+// ---------------------------------------------------------------------------
+// A block of NSW warps (NSW = 4 or 8) owns NSW systems j0 .. j0 + NSW - 1 and
+// takes chunks of 32 output sites.  Per chunk the warps first stage the 8
+// links of the 32 sites in shared memory, rebuilt to 18 reals (NSW = 4: warp w
+// the forward and backward link of direction w; NSW = 8: warp w link slot w),
+// together with the neighbour sites and signs of their direction; after a
+// block barrier warp w applies them to system j0 + w, one lane per site.  The
+// link loads, the row-2 rebuild and the index arithmetic are so paid once per
+// NSW systems instead of once per system, without holding a site's links in
+// registers for all of them.  FP32 links and vectors; epilogues EPI_CG_K1R and
+// EPI_CG_K2 exactly as in k_dslash (one lane per site); reductions per warp.
+template <int LP, int RECON, int NSW, int EPI>
+__global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
+  static_assert(LP == P32 && (NSW == 4 || NSW == 8) && (EPI == EPI_CG_K1R || EPI == EPI_CG_K2),
+                "FP32, 4 or 8 systems per block, the two CG kernels");
+  typedef float R;
+  constexpr int BT = 32 * NSW;
+  constexpr int NV = (EPI == EPI_CG_K2) ? 2 : 1;
+  const Geom g = a.g;
+  const int Ve = g.Ve;
+  const int G = a.ngroups;
+  const int grp = blockIdx.x % G, bx0 = blockIdx.x / G;
+  const int nbx = (int)gridDim.x / G;
+  const int nchunk = (Ve + 31) / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = grp * NSW, j = j0 + w;
+  const int P = a.par_out;
+  __shared__ float su[8][18][32];    // the chunk's links, rebuilt: [slot][real][site]
+  __shared__ int snb[8][32];         // neighbour site of slot (mu forward / mu backward)
+  __shared__ float ssg[8][32];       // its sign (eta, boundary; minus for the backward hop)
+  grid_dep_trigger();
+  grid_dep_wait();
+  __shared__ SysState sst[NSW];
+  const SysState *S = (a.ctl.st != nullptr) ? a.ctl.st + j0 : nullptr;
+  if (a.fold != FIN_NONE) {
+    fold_state<NSW, BT>(a, j0, bx0, sst);
+    S = sst;
+  }
+  const bool in = j < a.nsys;
+  const bool has = S != nullptr && in;
+  const bool act = in && (a.gate == GATE_NONE || !has || state_gate(S[w], a.gate));
+  const R m4 = (R)(has ? S[w].m4 : a.m4_single);
+  const R beta = (R)(has ? S[w].beta : 0.0);
+  const R alpha = (R)(has ? S[w].alpha : 0.0);
+  R part[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) part[v] = 0;
+
+  for (int bx = bx0; bx < nchunk; bx += nbx) {
+    const int s = bx * 32 + lane;
+    const bool valid = s < Ve;
+    __syncthreads();  // the previous chunk's links are no longer read
+    if (valid) {
+      int x[4];
+      site_coords(g, P, s, x);
+#pragma unroll
+      for (int q = 0; q < 8 / NSW; ++q) {
+        const int slot = (NSW == 4) ? (q == 0 ? w : 4 + w) : w;
+        const int mu = slot & 3;
+        const bool fwd = slot < 4;
+        const int Lmu = mu == 0 ? g.L0 : mu == 1 ? g.L1 : mu == 2 ? g.L2 : g.L3;
+        int eb = 0;  // x_0 + ... + x_{mu-1}
+        if (mu > 0) eb += x[0];
+        if (mu > 1) eb += x[1];
+        if (mu > 2) eb += x[2];
+        R sg = (eb & 1) ? R(-1) : R(1);
+        const int xm = x[mu];
+        int xn[4] = {x[0], x[1], x[2], x[3]};
+        xn[mu] = fwd ? ((xm + 1 == Lmu) ? 0 : xm + 1) : ((xm == 0) ? Lmu - 1 : xm - 1);
+        const int sn = cb_of(g, xn[0], xn[1], xn[2], xn[3]);
+        if (mu == 3 && g.ap && (fwd ? (xm == g.L3 - 1) : (xm == 0))) sg = -sg;
+        R u[18];
+        if (fwd) load_link<LP, RECON>(a.links, Ve, P, mu, s, u);
+        else load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sn, u);
+#pragma unroll
+        for (int e = 0; e < 18; ++e) su[slot][e][lane] = u[e];
+        snb[slot][lane] = sn;
+        ssg[slot][lane] = fwd ? sg : -sg;
+      }
+    }
+    __syncthreads();
+    if (!(act && valid)) continue;
+    // every load of the site for this system first, then the arithmetic
+    R vn[8][6];
+#pragma unroll
+    for (int slot = 0; slot < 8; ++slot) load_vec<P32>(a.in, j, snb[slot][lane], Ve, vn[slot]);
+    R c0[6], c1[6], c2[6];
+    if (EPI == EPI_CG_K2) {
+      load_vec_rw<P32>(a.center, j, s, Ve, c0);
+      load_vec_rw<P32>(a.aux, j, s, Ve, c1);
+      load_vec_rw<P32>(a.xlo, j, s, Ve, c2);
+    } else {
+      load_vec_rw<P32>(a.out, j, s, Ve, c0);
+    }
+    R acc[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int slot = 0; slot < 8; ++slot) {
+      R u[18];
+#pragma unroll
+      for (int e = 0; e < 18; ++e) u[e] = su[slot][e][lane];
+      if (slot < 4) mv_acc(u, vn[slot], ssg[slot][lane], acc);
+      else mvdag_acc(u, vn[slot], ssg[slot][lane], acc);
+    }
+    if (EPI == EPI_CG_K2) {
+      // p_new = r + beta p_old; Ap = 4 m^2 p_new - D_eo t; r -= alpha Ap; x_lo += alpha p_new
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        c0[i] = c1[i] + beta * c0[i];
+        const R ap = m4 * c0[i] - acc[i];
+        c1[i] -= alpha * ap;
+        c2[i] += alpha * c0[i];
+      }
+      R q = 0, rp = 0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        q += c1[i] * c1[i];
+        rp += c1[i] * c0[i];
+      }
+      part[0] += q;
+      part[NV - 1] += rp;
+      store_vec<P32>(a.center, j, s, Ve, c0);
+      store_vec<P32>(a.aux, j, s, Ve, c1);
+      store_vec<P32>(a.xlo, j, s, Ve, c2);
+    } else {
+      // t = D_oe r + beta t_old; |t|^2
+      R q = 0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        c0[i] = acc[i] + beta * c0[i];
+        q += c0[i] * c0[i];
+      }
+      part[0] += q;
+      store_vec<P32>(a.out, j, s, Ve, c0);
+    }
+  }
+  // one warp per system: its 32-lane sum is the block's partial
+  if (a.ctl.st != nullptr) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R t = warp_sum(part[v]);
+      if (lane == 0 && in) a.ctl.partials[((long long)j * NVMAX + v) * a.ctl.pstride + bx0] = (double)t;
+    }
   }
 }
 
