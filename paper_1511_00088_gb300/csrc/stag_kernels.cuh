@@ -1132,15 +1132,17 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
 // the two CG kernels for several systems, the links shared in shared memory
 // ---------------------------------------------------------------------------
 // A block of NSW warps (NSW = 4 or 8) owns NSW systems j0 .. j0 + NSW - 1 and
-// takes chunks of 32 output sites.  Per chunk the warps first stage the 8
-// links of the 32 sites in shared memory, rebuilt to 18 reals (NSW = 4: warp w
-// the forward and backward link of direction w; NSW = 8: warp w link slot w),
-// together with the neighbour sites and signs of their direction; after a
-// block barrier warp w applies them to system j0 + w, one lane per site.  The
-// link loads, the row-2 rebuild and the index arithmetic are so paid once per
-// NSW systems instead of once per system, without holding a site's links in
-// registers for all of them.  FP32 links and vectors; epilogues EPI_CG_K1R and
-// EPI_CG_K2 exactly as in k_dslash (one lane per site); reductions per warp.
+// takes chunks of 32 output sites.  The 8 links of a chunk's sites go into
+// shared memory once for all NSW systems (NSW = 4: warp w copies the forward
+// and the backward link of direction w; NSW = 8: warp w link slot w), with the
+// neighbour sites and signs of the slot; warp w then applies them to system
+// j0 + w, one lane per site.  The link loads, the row-2 rebuild and the index
+// arithmetic are so paid once per NSW systems, without holding a site's links
+// in registers for all of them.  Two buffers: while a chunk is computed, the
+// next chunk's links arrive by asynchronous copies (cp.async, no registers),
+// and each chunk's gathered vectors are loaded before the barriers that make
+// its links ready.  FP32 links and vectors; epilogues EPI_CG_K1R and EPI_CG_K2
+// exactly as in k_dslash (one lane per site); reductions per warp.
 template <int LP, int RECON, int NSW, int EPI>
 __global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
   static_assert(LP == P32 && (NSW == 4 || NSW == 8) && (EPI == EPI_CG_K1R || EPI == EPI_CG_K2),
@@ -1157,9 +1159,10 @@ __global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j0 = grp * NSW, j = j0 + w;
   const int P = a.par_out;
-  __shared__ float su[8][18][32];    // the chunk's links, rebuilt: [slot][real][site]
-  __shared__ int snb[8][32];         // neighbour site of slot (mu forward / mu backward)
-  __shared__ float ssg[8][32];       // its sign (eta, boundary; minus for the backward hop)
+  constexpr int NEL = RECON ? 6 : 9;  // stored complex elements per link
+  __shared__ __align__(16) float2 su[2][8][9][32];  // [buffer][slot][element][site]
+  __shared__ int snb[2][8][32];                      // neighbour site of the slot
+  __shared__ float ssg[2][8][32];                    // its sign (minus for backward hops)
   grid_dep_trigger();
   grid_dep_wait();
   __shared__ SysState sst[NSW];
@@ -1177,12 +1180,14 @@ __global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
   R part[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) part[v] = 0;
+  typedef typename Tr<LP>::S2 LS2;
+  const LS2 *lk = reinterpret_cast<const LS2 *>(a.links);
 
-  for (int bx = bx0; bx < nchunk; bx += nbx) {
+  // this warp's slots of chunk bx into buffer b: indices, signs, and the
+  // stored link elements by asynchronous copies (one commit group per call)
+  auto stage = [&](int bx, int b) {
     const int s = bx * 32 + lane;
-    const bool valid = s < Ve;
-    __syncthreads();  // the previous chunk's links are no longer read
-    if (valid) {
+    if (s < Ve) {
       int x[4];
       site_coords(g, P, s, x);
 #pragma unroll
@@ -1201,37 +1206,76 @@ __global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
         xn[mu] = fwd ? ((xm + 1 == Lmu) ? 0 : xm + 1) : ((xm == 0) ? Lmu - 1 : xm - 1);
         const int sn = cb_of(g, xn[0], xn[1], xn[2], xn[3]);
         if (mu == 3 && g.ap && (fwd ? (xm == g.L3 - 1) : (xm == 0))) sg = -sg;
-        R u[18];
-        if (fwd) load_link<LP, RECON>(a.links, Ve, P, mu, s, u);
-        else load_link<LP, RECON>(a.links, Ve, 1 - P, mu, sn, u);
+        snb[b][slot][lane] = sn;
+        ssg[b][slot][lane] = fwd ? sg : -sg;
+        const LS2 *src = lk + (long long)(((fwd ? P : 1 - P) * 4 + mu) * NEL) * Ve + (fwd ? s : sn);
 #pragma unroll
-        for (int e = 0; e < 18; ++e) su[slot][e][lane] = u[e];
-        snb[slot][lane] = sn;
-        ssg[slot][lane] = fwd ? sg : -sg;
+        for (int e = 0; e < NEL; ++e)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(&su[b][slot][e][lane])),
+                       "l"(src + (long long)e * Ve)
+                       : "memory");
       }
     }
-    __syncthreads();
-    if (!(act && valid)) continue;
-    // every load of the site for this system first, then the arithmetic
-    R vn[8][6];
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  if (bx0 < nchunk) stage(bx0, 0);
+  int b = 0;
+  for (int bx = bx0; bx < nchunk; bx += nbx, b ^= 1) {
+    const int s = bx * 32 + lane;
+    const bool valid = s < Ve;
+    __syncthreads();  // buffer b's indices visible; nobody still reads buffer b ^ 1
+    // this chunk's gathered and centre vectors, in flight across the barriers below
+    R vn[8][6], c0[6], c1[6], c2[6];
+    if (act && valid) {
 #pragma unroll
-    for (int slot = 0; slot < 8; ++slot) load_vec<P32>(a.in, j, snb[slot][lane], Ve, vn[slot]);
-    R c0[6], c1[6], c2[6];
-    if (EPI == EPI_CG_K2) {
-      load_vec_rw<P32>(a.center, j, s, Ve, c0);
-      load_vec_rw<P32>(a.aux, j, s, Ve, c1);
-      load_vec_rw<P32>(a.xlo, j, s, Ve, c2);
-    } else {
-      load_vec_rw<P32>(a.out, j, s, Ve, c0);
+      for (int slot = 0; slot < 8; ++slot) load_vec<P32>(a.in, j, snb[b][slot][lane], Ve, vn[slot]);
+      if (EPI == EPI_CG_K2) {
+        load_vec_rw<P32>(a.center, j, s, Ve, c0);
+        load_vec_rw<P32>(a.aux, j, s, Ve, c1);
+        load_vec_rw<P32>(a.xlo, j, s, Ve, c2);
+      } else {
+        load_vec_rw<P32>(a.out, j, s, Ve, c0);
+      }
     }
+    if (bx + nbx < nchunk) stage(bx + nbx, b ^ 1);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of chunk bx
+    __syncthreads();                                      // everybody's
+    if (RECON && valid) {
+      // row 2 = conj(row0 x row1) for this warp's slots, in place
+#pragma unroll
+      for (int q = 0; q < 8 / NSW; ++q) {
+        const int slot = (NSW == 4) ? (q == 0 ? w : 4 + w) : w;
+        float2 r0[3], r1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          r0[c] = su[b][slot][c][lane];
+          r1[c] = su[b][slot][3 + c][lane];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int i1 = (c + 1) % 3, i2 = (c + 2) % 3;
+          const float re = (r0[i1].x * r1[i2].x - r0[i1].y * r1[i2].y) - (r0[i2].x * r1[i1].x - r0[i2].y * r1[i1].y);
+          const float im = (r0[i1].x * r1[i2].y + r0[i1].y * r1[i2].x) - (r0[i2].x * r1[i1].y + r0[i2].y * r1[i1].x);
+          su[b][slot][6 + c][lane] = make_float2(re, -im);
+        }
+      }
+    }
+    if (RECON) __syncthreads();
+    if (!(act && valid)) continue;
     R acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
       R u[18];
 #pragma unroll
-      for (int e = 0; e < 18; ++e) u[e] = su[slot][e][lane];
-      if (slot < 4) mv_acc(u, vn[slot], ssg[slot][lane], acc);
-      else mvdag_acc(u, vn[slot], ssg[slot][lane], acc);
+      for (int e = 0; e < 9; ++e) {
+        const float2 v2 = su[b][slot][e][lane];
+        u[2 * e] = v2.x;
+        u[2 * e + 1] = v2.y;
+      }
+      if (slot < 4) mv_acc(u, vn[slot], ssg[b][slot][lane], acc);
+      else mvdag_acc(u, vn[slot], ssg[b][slot][lane], acc);
     }
     if (EPI == EPI_CG_K2) {
       // p_new = r + beta p_old; Ap = 4 m^2 p_new - D_eo t; r -= alpha Ap; x_lo += alpha p_new
@@ -1265,6 +1309,7 @@ __global__ void __launch_bounds__(32 * NSW, 1) k_dslash_mrhs(const DsArgs a) {
       store_vec<P32>(a.out, j, s, Ve, c0);
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");  // none outstanding at exit
   // one warp per system: its 32-lane sum is the block's partial
   if (a.ctl.st != nullptr) {
 #pragma unroll
