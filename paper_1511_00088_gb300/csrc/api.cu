@@ -412,7 +412,7 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
 // each (1 or 2) and, where allowed (tma_ok: one system, reduced-precision
 // links), the link path of both (DsArgs::tma, among c->tma_modes); whether
 // their links persist in L2 follows a rule (below).  Each candidate
-// runs 20 alternating launch pairs with the solver's grids, twice (the second
+// runs tune_pairs() alternating launch pairs with the solver's grids, twice (the second
 // sweep in reverse order), and the fastest total wins: the iteration
 // alternates the two kernels, each starting on the cache state the other
 // leaves.  Cached as 1000 l2p + 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2
@@ -436,8 +436,9 @@ int mrhs_blocks(stag_ctx *c, int recon, int nsw, int EPI, int G, int *nbx) {
   return STAG_OK;
 }
 
-// total time of 2 x 20 alternating launch pairs of the two k_dslash_mrhs CG
-// kernels with nsw systems per block (the measure tune_cg_pair reports)
+// total time of 2 sweeps of tune_pairs() alternating launch pairs of the two
+// k_dslash_mrhs CG kernels with nsw systems per block (the measure
+// tune_cg_pair reports)
 int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float *ms_out) {
   const int G = (a1.nsys + nsw - 1) / nsw;
   a1.ngroups = a2.ngroups = G;
@@ -448,8 +449,9 @@ int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float 
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float tot = 0.f;
+  const int np = tune_pairs(c);
   for (int o = 0; o < 2; ++o) {
-    for (int i = 0; i < 22; ++i) {
+    for (int i = 0; i < np + 2; ++i) {
       if (i == 2) CK(cudaEventRecord(e0, c->stream));
       CK(launch_dslash_mrhs(P32, recon, nsw, EPI_CG_K1R, n1 * G, c->stream, a1));
       CK(launch_dslash_mrhs(P32, recon, nsw, EPI_CG_K2, n2 * G, c->stream, a2));
@@ -464,6 +466,14 @@ int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float 
   cudaEventDestroy(e1);
   *ms_out = tot;
   return STAG_OK;
+}
+
+// alternating launch pairs per timed sweep of the tuner: 20 at 20^3 x 64 and
+// below, fewer on larger lattices (at least 3), so that tuning stays well under
+// a second of kernel time
+int tune_pairs(const stag_ctx *c) {
+  const double n = 20.0 * 256000.0 / (double)c->Ve;
+  return n >= 20.0 ? 20 : n <= 3.0 ? 3 : (int)n;
 }
 
 struct CgForm {
@@ -551,7 +561,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
     set_l2_window(c, LP, f.tma, f.l2p, a1);
     set_l2_window(c, LP, f.tma, f.l2p, a2);
     if (f.l2p) l2_setaside(c, true);
-    for (int i = 0; i < 22; ++i) {
+    for (int i = 0; i < tune_pairs(c) + 2; ++i) {
       if (i == 2) CK(cudaEventRecord(e0, c->stream));
       CK(launch_dslash(LP, recon, VP, VP, NS, EPI1, f.l1, nb1[q], c->stream, a1));
       CK(launch_dslash(LP, recon, VP, VP, NS, EPI_CG_K2, f.l2, nb2[q], c->stream, a2));
