@@ -417,6 +417,14 @@ int cg_blocks(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI, int lanes
 // alternates the two kernels, each starting on the cache state the other
 // leaves.  Cached as 1000 l2p + 100 tma + 10 l1 + l2.  STAG_LANES = 1 or 2
 // fixes the lanes.
+// alternating launch pairs per timed sweep of the tuner: 20 at 20^3 x 64 and
+// below, fewer on larger lattices (at least 3), so that tuning stays well under
+// a second of kernel time
+int tune_pairs(const stag_ctx *c) {
+  const double n = 20.0 * 256000.0 / (double)c->Ve;
+  return n >= 20.0 ? 20 : n <= 3.0 ? 3 : (int)n;
+}
+
 // Blocks per system group of k_dslash_mrhs with nsw systems per block: one
 // wave of resident blocks, at most one per 32-site chunk.
 int mrhs_blocks(stag_ctx *c, int recon, int nsw, int EPI, int G, int *nbx) {
@@ -466,14 +474,6 @@ int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float 
   cudaEventDestroy(e1);
   *ms_out = tot;
   return STAG_OK;
-}
-
-// alternating launch pairs per timed sweep of the tuner: 20 at 20^3 x 64 and
-// below, fewer on larger lattices (at least 3), so that tuning stays well under
-// a second of kernel time
-int tune_pairs(const stag_ctx *c) {
-  const double n = 20.0 * 256000.0 / (double)c->Ve;
-  return n >= 20.0 ? 20 : n <= 3.0 ? 3 : (int)n;
 }
 
 struct CgForm {
