@@ -191,6 +191,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def whole_job(dist, ms_step, flops_step, device):
+    """Whole-job numbers of the replicas: the step time is the slowest rank's
+    (max over ranks), the work is every rank's (sum); without a process group
+    the rank's own.  Returns (ms_per_step, flops_per_step, GFLOP/s)."""
+    flops_all = flops_step
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms_step], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        f = torch.tensor([flops_step], device=device, dtype=torch.float64)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        flops_all = float(f.item())
+    return ms_step, flops_all, flops_all / (ms_step * 1e-3) / 1e9
+
+
+def sum_over_ranks(dist, value, device):
+    """A throughput summed over the replicas (None stays None)."""
+    if dist is None or value is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def cpu_oracle_sample(L, U, b, mass, budget_s):
     """The FP64 oracle's CG for a bounded number of iterations on this workload."""
     import oracle
@@ -323,16 +349,7 @@ def run_ours(args):
     form = ctx.solve_form()
     ms_step = total_ms / args.steps
     flops_step = FLOP_PER_SITE_ITER * Ve * statistics.mean(sum(i) for i in iters)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-        f = torch.tensor([flops_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(f, op=dist.ReduceOp.SUM)
-        flops_all = float(f.item())
-    else:
-        flops_all = flops_step
-    value = flops_all / (ms_step * 1e-3) / 1e9
+    ms_step, flops_all, value = whole_job(dist, ms_step, flops_step, "cuda")
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     bhs = [torch.from_numpy(v).pin_memory() for v in bs]
@@ -349,10 +366,7 @@ def run_ours(args):
     e2e_ms_step = statistics.mean(e2e_ms) if e2e_ms else None
     e2e_value = (FLOP_PER_SITE_ITER * Ve * statistics.mean(e2e_it) / (e2e_ms_step * 1e-3) / 1e9
                  if e2e_ms else None)
-    if dist and e2e_value is not None:
-        t = torch.tensor([e2e_value], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_value = float(t.item())
+    e2e_value = sum_over_ranks(dist, e2e_value, "cuda")
 
     # the two CG kernels, timed alternately as the iteration runs them (CUDA
     # events between launches); the roofline is reported for the slower one
