@@ -1,8 +1,12 @@
-// P16 link-storage instantiations of the half operator: Krylov vectors at
-// FP32 (the default solver and the operator calls of the C ABI) or at P16
-// with a per-site scale (STAG_HALF_VECTORS, STAG_ROUND_OUTPUT).
+// P16 link-storage instantiations of the half operator with FP32 Krylov
+// vectors (the default solver and the operator calls of the C ABI); the
+// P16-vector ones (STAG_HALF_VECTORS, STAG_ROUND_OUTPUT) are in
+// dslash_p16h.cu, compiled in parallel.
 #include "dslash_inst.cuh"
 namespace stag {
+cudaError_t launch_dslash_p16h(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
+                               cudaStream_t st, const DsArgs &a, const void **kptr);
+
 cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a, const void **kptr) {
   STAG_DS_EPIS(P16, 0, P32, P32, 1)
@@ -11,12 +15,6 @@ cudaError_t launch_dslash_p16(int recon, int VP, int OP, int NS, int EPI, int la
   STAG_DS_EPIS(P16, 1, P32, P32, 1)
   STAG_DS_EPIS(P16, 1, P32, P32, 4)
   STAG_DS_EPIS(P16, 1, P32, P32, 8)
-  STAG_DS_EPIS(P16, 0, P16, P16, 1)
-  STAG_DS_EPIS(P16, 0, P16, P16, 4)
-  STAG_DS_EPIS(P16, 0, P16, P16, 8)
-  STAG_DS_EPIS(P16, 1, P16, P16, 1)
-  STAG_DS_EPIS(P16, 1, P16, P16, 4)
-  STAG_DS_EPIS(P16, 1, P16, P16, 8)
-  return cudaErrorNotSupported;
+  return launch_dslash_p16h(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
 }
 }  // namespace stag

@@ -1,8 +1,12 @@
-// PBF link-storage instantiations of the half operator: Krylov vectors at
-// FP32 (the default solver and the operator calls of the C ABI) or at PBF
-// with a per-site scale (STAG_HALF_VECTORS, STAG_ROUND_OUTPUT).
+// PBF link-storage instantiations of the half operator with FP32 Krylov
+// vectors (the default solver and the operator calls of the C ABI); the
+// PBF-vector ones (STAG_HALF_VECTORS, STAG_ROUND_OUTPUT) are in
+// dslash_pbfh.cu, compiled in parallel.
 #include "dslash_inst.cuh"
 namespace stag {
+cudaError_t launch_dslash_pbfh(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
+                               cudaStream_t st, const DsArgs &a, const void **kptr);
+
 cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int lanes, int nblocks,
                               cudaStream_t st, const DsArgs &a, const void **kptr) {
   STAG_DS_EPIS(PBF, 0, P32, P32, 1)
@@ -11,12 +15,6 @@ cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int la
   STAG_DS_EPIS(PBF, 1, P32, P32, 1)
   STAG_DS_EPIS(PBF, 1, P32, P32, 4)
   STAG_DS_EPIS(PBF, 1, P32, P32, 8)
-  STAG_DS_EPIS(PBF, 0, PBF, PBF, 1)
-  STAG_DS_EPIS(PBF, 0, PBF, PBF, 4)
-  STAG_DS_EPIS(PBF, 0, PBF, PBF, 8)
-  STAG_DS_EPIS(PBF, 1, PBF, PBF, 1)
-  STAG_DS_EPIS(PBF, 1, PBF, PBF, 4)
-  STAG_DS_EPIS(PBF, 1, PBF, PBF, 8)
-  return cudaErrorNotSupported;
+  return launch_dslash_pbfh(recon, VP, OP, NS, EPI, lanes, nblocks, st, a, kptr);
 }
 }  // namespace stag
