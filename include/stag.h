@@ -48,6 +48,7 @@ extern "C" {
 #define STAG_ERR_OOM (-3)    /* device allocation failed */
 #define STAG_ERR_NOT_SU3 (-4) /* reconstruct-12 requested on links that are not SU(3) */
 #define STAG_ERR_BREAKDOWN (-5) /* <p, A p> <= 0 or a non-finite residual in CG */
+#define STAG_ERR_TIMEOUT (-6) /* a bounded device-side wait gave up; the results are void */
 #define STAG_ERR_STATE (-7)  /* operator used before stag_links_upload */
 
 /* arithmetic/storage precision of the inner (Krylov) iteration */
@@ -137,7 +138,9 @@ int stag_mdagm(stag_ctx *ctx, int precision, double mass, const double *in_even,
  * A zero source gives x = 0, 0 iterations, true_res = 0.
  * Returns STAG_OK when every system converged, STAG_NOT_CONVERGED when some
  * system hit maxiter (its x is the last iterate), STAG_ERR_BREAKDOWN on a
- * non-positive <p, A p> or a non-finite residual, STAG_ERR_ARG / _STATE / _CUDA.
+ * non-positive <p, A p> or a non-finite residual, STAG_ERR_TIMEOUT when a
+ * kernel's bounded wait for its staged links gave up (only with the
+ * shared-memory link path, STAG_TMA=1), STAG_ERR_ARG / _STATE / _CUDA.
  */
 int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const double masses[],
                   int nmass, double tol, int maxiter, int precision, double *const x[],

@@ -1215,7 +1215,7 @@ int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[])
   cudaGetLastError();
   if (hf[4] != 0) {
     c->err = "a CG kernel gave up waiting for its bulk-copied links; the solution is void";
-    return STAG_ERR_CUDA;
+    return STAG_ERR_TIMEOUT;
   }
   int status = STAG_OK;
   for (int j = 0; j < nsys; ++j) {
@@ -1464,6 +1464,7 @@ const char *stag_status_string(int s) {
     case STAG_ERR_OOM: return "STAG_ERR_OOM";
     case STAG_ERR_NOT_SU3: return "STAG_ERR_NOT_SU3";
     case STAG_ERR_BREAKDOWN: return "STAG_ERR_BREAKDOWN";
+    case STAG_ERR_TIMEOUT: return "STAG_ERR_TIMEOUT";
     case STAG_ERR_STATE: return "STAG_ERR_STATE";
   }
   return "STAG_UNKNOWN_STATUS";

@@ -25,6 +25,7 @@ STAG_ERR_CUDA = -2
 STAG_ERR_OOM = -3
 STAG_ERR_NOT_SU3 = -4
 STAG_ERR_BREAKDOWN = -5
+STAG_ERR_TIMEOUT = -6
 STAG_ERR_STATE = -7
 
 STAG_FP64, STAG_FP32, STAG_FP16, STAG_BF16 = 0, 1, 2, 3
