@@ -355,11 +355,18 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // wait until the phase with parity `parity` of the barrier has completed;
-// gives up (false) after 2^20 polls, each of which the hardware may suspend
-// for a bounded time
+// gives up (false) after about a second (the global timer, checked every 64
+// polls) or 2^20 polls, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
   const uint32_t b = smem_addr(bar);
+  const unsigned long long t0 = global_ns();
   for (int i = 0; i < (1 << 20); ++i) {
     uint32_t ok;
     asm volatile(
@@ -368,6 +375,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
         : "r"(b), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((i & 63) == 63 && global_ns() - t0 > 1000000000ull) return false;
   }
   return false;
 }
@@ -791,6 +799,7 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
   constexpr unsigned CHUNK = (unsigned)(SPB * 8 * NEL * sizeof(LS2));
   extern __shared__ __align__(128) unsigned char stage_mem[];
   __shared__ __align__(8) uint64_t stage_bar[NSTG];
+  __shared__ volatile int stage_failed;  // a bounded wait of this block gave up
   const int nmine = bx0 < nchunk ? (nchunk - 1 - bx0) / nbx + 1 : 0;  // chunks of this block
   auto issue = [&](int q) {  // bulk copy of this block's chunk q into stage q % NSTG
     const LS2 *src = reinterpret_cast<const LS2 *>(a.links_tile) +
@@ -801,6 +810,7 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
     if (threadIdx.x == 0) {
       for (int q = 0; q < NSTG; ++q) mbar_init(&stage_bar[q], 1);
       fence_mbar_init();
+      stage_failed = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -844,8 +854,10 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
       fence_proxy_async_smem();
       issue(round + NSTG - 1);
     }
-    if (!mbar_wait(&stage_bar[round % NSTG], (unsigned)(round / NSTG) & 1u) && a.ctl.flags != nullptr)
-      atomicExch(a.ctl.flags + 4, 1);  // reported by the host; the round's results are void
+    if (!stage_failed && !mbar_wait(&stage_bar[round % NSTG], (unsigned)(round / NSTG) & 1u)) {
+      stage_failed = 1;  // this block waits no more; the host reports the error
+      if (a.ctl.flags != nullptr) atomicExch(a.ctl.flags + 4, 1);
+    }
     lsm = reinterpret_cast<const LS2 *>(stage_mem + (round % NSTG) * CHUNK);
   }
   const int s = bx * SPB + (int)(threadIdx.x / LANES);
@@ -1122,6 +1134,16 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
     }
   }
   }  // chunks
+  if (TMA == 1) {
+    __syncthreads();  // every thread's stage_failed visible: the branch below is uniform
+    if (stage_failed) {
+      // copies that may still be in flight land before the block exits
+      // (bounded again; the results of this launch are void in any case)
+      if (threadIdx.x == 0)
+        for (int q = 0; q < NSTG; ++q) mbar_wait(&stage_bar[q], 0u), mbar_wait(&stage_bar[q], 1u);
+      __syncthreads();
+    }
+  }
 
   if (EPI == EPI_CG_K1 || EPI == EPI_CG_K1R || EPI == EPI_CG_K2 || EPI == EPI_RESID) {
     if (a.ctl.st != nullptr) block_partials<NS, NV>(a.ctl, part, j0, a.nsys, bx0);
