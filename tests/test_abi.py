@@ -55,3 +55,17 @@ def test_create_rejects_bad_dims_before_touching_cuda(lib, dims):
 def test_create_rejects_unknown_flags(lib):
     st, h = stag.stag_create((4, 4, 4, 4), 1 << 7, None)
     assert st == stag.STAG_ERR_ARG
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_header_is_plain_c_and_cxx(lang, std):
+    """include/stag.h compiles on its own as C99 and as C++11 (no CUDA or
+    torch types in the boundary)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang, HEADER],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
