@@ -864,7 +864,8 @@ cudaError_t launch_cg(stag_ctx *c, int kernel, int epi, cudaStream_t s, const Ds
   return launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi, kernel == 0 ? w.lanes_k1 : w.lanes_k2, nb, s, a);
 }
 
-// K1..K3
+// One CG iteration with a finalize kernel after each CG kernel (the form
+// without folded reductions, STAG_FOLD=0): K1, its finalize, K2, its finalize.
 int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   Work &w = c->w;
   const void *lo = nullptr;
@@ -981,7 +982,8 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
   return STAG_OK;
 }
 
-// K4..K6 (the reliable update; every kernel gated per system)
+// The reliable update (K4..K6 of the header comment; every kernel gated per
+// system: only systems with an update due take part)
 int enqueue_update(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   Work &w = c->w;
   BlasArgs b = blas_base(c, ctl);
