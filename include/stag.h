@@ -148,8 +148,8 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
 
 /*
  * Average device time of one launch of one of the two half-operator kernels
- * of the CG iteration (Sec. 3, the even-odd operator of Eq. 2 split as
- * A p = 4 m^2 p - D_eo (D_oe p)) at `precision`, measured with CUDA events
+ * of the CG iteration (Sec. 3; the operator A of the top of this header, split
+ * as A p = 4 m^2 p - D_eo (D_oe p)) at `precision`, measured with CUDA events
  * on the context stream over `nlaunch` pairs of the two kernels launched
  * alternately, as the iteration runs them (each starts on the cache state the
  * other leaves), on the context's own internal vectors with the solver's
