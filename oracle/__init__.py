@@ -61,6 +61,7 @@ def _bind(path):
         "orc_mdagm": (None, [P, I, P, D, P, P]),
         "orc_true_residual": (D, [P, I, P, D, P, P]),
         "orc_cg": (I, [P, I, P, D, P, P, D, I, P, P]),
+        "orc_solve_full": (I, [P, I, P, D, P, P, D, I, P, P]),
         "orc_round_format": (D, [D, I, I]),
         "orc_quantize_vectors": (None, [I, L, P, P]),
         "orc_round_links": (None, [I, L, P, P]),
@@ -190,6 +191,19 @@ def cg(L, links, mass, b, tol=1e-10, maxiter=100000, antiperiodic=True):
     tr = ctypes.c_double(0.0)
     st = lib.orc_cg(_p(d), int(antiperiodic), _p(U), float(mass), _p(bb), _p(x), float(tol),
                     int(maxiter), ctypes.byref(it), ctypes.byref(tr))
+    return x, int(st), int(it.value), float(tr.value)
+
+
+def solve_full(L, links, mass, b_full, tol=1e-12, maxiter=100000, antiperiodic=True):
+    """M x = b on the whole lattice, M = 2m + D, by the even-odd Schur route.
+    b_full (V, 3).  Returns (x_full, status, iters, true_res of the even system)."""
+    lib = _load()
+    d, U, bb = _dims(L), _c128(links), _c128(b_full)
+    x = np.empty_like(bb)
+    it = ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    st = lib.orc_solve_full(_p(d), int(antiperiodic), _p(U), float(mass), _p(bb), _p(x), float(tol),
+                            int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     return x, int(st), int(it.value), float(tr.value)
 
 

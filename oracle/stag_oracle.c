@@ -282,6 +282,41 @@ int orc_cg(const int L[4], int antiperiodic, const double *U, double mass, const
     return status;
 }
 
+/*
+ * The full-lattice staggered equation M x = b with M = 2m + D (the equation
+ * the inverter of Sec. 3 solves; the even-site CG above is its Schur
+ * complement).  With M = [[2m, D_eo], [D_oe, 2m]] on (even, odd):
+ *   (4m^2 - D_eo D_oe) x_e = 2m b_e - D_eo b_o   (orc_cg),
+ *   x_o = (b_o - D_oe x_e) / (2m).
+ * b and x are full vectors [V][3] complex; mass > 0.  Returns orc_cg's
+ * status, with its iterations and the true residual of the even system.
+ */
+int orc_solve_full(const int L[4], int antiperiodic, const double *U, double mass, const double *b,
+                   double *x, double tol, int maxiter, int *iters_out, double *true_res_out)
+{
+    long n = 6 * (volume(L) / 2);
+    double *be = (double *)malloc(sizeof(double) * n);
+    double *bo = (double *)malloc(sizeof(double) * n);
+    double *bt = (double *)malloc(sizeof(double) * n);
+    double *xe = (double *)malloc(sizeof(double) * n);
+    double *xo = (double *)malloc(sizeof(double) * n);
+    double *t = (double *)malloc(sizeof(double) * n);
+    orc_gather_parity(L, 0, b, be);
+    orc_gather_parity(L, 1, b, bo);
+    orc_dslash_eo(L, antiperiodic, U, bo, t);
+    for (long k = 0; k < n; ++k) bt[k] = 2.0 * mass * be[k] - t[k];
+    int status = orc_cg(L, antiperiodic, U, mass, bt, xe, tol, maxiter, iters_out, true_res_out);
+    orc_dslash_oe(L, antiperiodic, U, xe, t);
+    for (long k = 0; k < n; ++k) xo[k] = (bo[k] - t[k]) / (2.0 * mass);
+    /* each scatter zeroes the other parity: combine two full vectors */
+    double *xf = (double *)malloc(sizeof(double) * 2 * n);
+    orc_scatter_parity(L, 0, xe, x);
+    orc_scatter_parity(L, 1, xo, xf);
+    for (long k = 0; k < 2 * n; ++k) x[k] += xf[k];
+    free(be); free(bo); free(bt); free(xe); free(xo); free(t); free(xf);
+    return status;
+}
+
 /* ------------------------------------------------------------------ */
 /* reduced-precision storage (test reference for quantised inputs)      */
 /* ------------------------------------------------------------------ */

@@ -56,6 +56,12 @@ MUTANTS = {
         "cplx t1 = c_mul(P2[j * 3 + a], c_conj(P1[i * 3 + b]));",
         "cplx t1 = c_mul(P2[j * 3 + b], c_conj(P1[i * 3 + a]));"),
     "Lie projection sign": ("f[n * 8 + g] = -0.5 * tr.im;", "f[n * 8 + g] = 0.5 * tr.im;"),
+    "full solve: odd source added to the even one": (
+        "bt[k] = 2.0 * mass * be[k] - t[k];", "bt[k] = 2.0 * mass * be[k] + t[k];"),
+    "full solve: even source without 2m": (
+        "bt[k] = 2.0 * mass * be[k] - t[k];", "bt[k] = be[k] - t[k];"),
+    "full solve: odd sites without 1/(2m)": (
+        "xo[k] = (bo[k] - t[k]) / (2.0 * mass);", "xo[k] = (bo[k] - t[k]) / mass;"),
 }
 
 
@@ -69,6 +75,7 @@ def _pins():
     yield lambda: sv.test_cg_matches_dense_solve((2, 2, 2, 2), 0.05, 0.7)
     yield lambda: sv.test_cg_degenerate_cases()
     yield lambda: sv.test_force_central_differences((2, 2, 2, 4))
+    yield lambda: sv.test_full_lattice_solve_matches_dense((2, 2, 2, 2), 0.05, 0.7)
 
 
 @pytest.fixture(scope="module")

@@ -182,3 +182,25 @@ def test_round_links_matches_library_rounding(prec):
     else:
         ref = torch.from_numpy(f).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(got.view(np.float64), ref)
+
+
+@pytest.mark.parametrize("L,m,c", [((2, 2, 2, 2), 0.05, 0.7), ((4, 2, 2, 4), 0.1, 0.4)])
+def test_full_lattice_solve_matches_dense(L, m, c):
+    """M x = b on the whole lattice (M = 2m + D) by the even-odd Schur route
+    equals a dense LU solve of the assembled M."""
+    V = synth.volume(L)
+    U = synth.random_links(L, c, 111)
+    b = synth.gaussian_vector(V, 112)
+    n = 3 * V
+    M = np.empty((n, n), np.complex128)
+    e = np.zeros(n, np.complex128)
+    for j in range(n):
+        e[:] = 0
+        e[j] = 1
+        M[:, j] = 2 * m * e + oracle.dslash_full(L, U, e.reshape(-1, 3)).reshape(-1)
+    xd = np.linalg.solve(M, b.reshape(-1)).reshape(-1, 3)
+    x, st, it, tr = oracle.solve_full(L, U, m, b, tol=1e-13)
+    assert st == 0
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10
+    r = 2 * m * x + oracle.dslash_full(L, U, x) - b
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-11
