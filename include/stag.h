@@ -243,7 +243,8 @@ int stag_solve_form(const stag_ctx *ctx, int out[8]);
  *     device); make it before any stream capture;
  *   - all calls share the array: calls that overlap on the GPU race;
  *   - asynchronous: results are ready when the context's stream reaches them.
- * Errors: STAG_ERR_ARG (size, NULL or host pointer), STAG_ERR_STATE (no links),
+ * Errors: STAG_ERR_ARG (size, NULL pointer, host memory or another GPU's
+ * memory; managed memory is accepted), STAG_ERR_STATE (no links),
  * STAG_ERR_CUDA.
  */
 int stag_mdagm_dot_noalloc(stag_ctx *ctx, double mass, const double *in_even, double *tmp_odd,

@@ -178,6 +178,9 @@ struct stag_ctx {
   bool fold = true;     // each CG kernel finishes its predecessor's reduction itself
   bool persist = true;  // CG kernels launched as one wave of resident blocks
   int tma_modes = 0b101;  // link paths (bit t: DsArgs::tma = t) the tuner may choose for one system
+  // STAG_TEST_WAIT_GIVEUP=1: in the solve loop, the bounded waits of the
+  // shared-memory link path give up at once (tests of the failure path)
+  int wait_giveup = 0;
   // L2 residency of the inner-precision links during a solve: the CG kernels
   // mark them as an access-policy window whose lines persist in L2 (the rest
   // of their traffic streams), so of the two passes over the links per
@@ -881,6 +884,7 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
   a.pdl = c->pdl ? 1 : 0;
   if (w.tma) CKS(links_tile_for(c, w.prec, &w.links_tile));
   a.tma = w.tma;
+  a.wait_giveup = c->wait_giveup;
   a.links_tile = w.links_tile;
   a.ntile = link_tiles(c->Ve);
   set_l2_window(c, w.prec, w.tma, w.l2p, a);
@@ -942,6 +946,7 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
   a.pdl = c->pdl ? 1 : 0;
   if (w.tma) CKS(links_tile_for(c, w.prec, &w.links_tile));
   a.tma = w.tma;
+  a.wait_giveup = c->wait_giveup;
   a.links_tile = w.links_tile;
   a.ntile = link_tiles(c->Ve);
   set_l2_window(c, w.prec, w.tma, w.l2p, a);
@@ -1437,12 +1442,10 @@ int ragged_impl(const stag_solve_desc *d, int n, double tol, int maxiter, int pr
 
 // Internal accessors used by noalloc.cu (not part of the C ABI).
 namespace stag {
-int ctx_fp64_links(const stag_ctx *c, const void **links, Geom *g, cudaStream_t *stream, int *device) {
+int ctx_fp64_links(const stag_ctx *c, const void **links, cudaStream_t *stream) {
   if (!c->have_links) return STAG_ERR_STATE;
   *links = c->links64.p;
-  *g = c->g;
   *stream = c->stream;
-  *device = c->device;
   return STAG_OK;
 }
 void ctx_set_error(stag_ctx *c, const char *msg) { c->err = msg; }
@@ -1519,6 +1522,8 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
   // memory caps the sites in flight per SM below what the registers hold)
   if (tma && (tma[0] == '0' || tma[0] == '1' || tma[0] == '2') && tma[1] == 0) c->tma_modes = 1 << (tma[0] - '0');
   else if (tma && tma[0] == 't' && tma[1] == 0) c->tma_modes = 0b111;
+  const char *giveup = getenv("STAG_TEST_WAIT_GIVEUP");
+  c->wait_giveup = (giveup && giveup[0] == '1') ? 1 : 0;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -122,6 +122,9 @@ __global__ void __launch_bounds__(FIN_BT) k_finalize(const Ctl c, int fin, int n
     if (passes > c.flags[3]) running = 0;
   }
   if (fin == FIN_RESID) c.flags[5] += 1;  // executions of the reliable-update step
+  // a CG kernel gave up waiting for its staged links: the iterates are void,
+  // so the loop and the update stop here and the host reports the timeout
+  if (*(volatile int *)(c.flags + 4) != 0) running = upd = 0;
   c.flags[0] = running;
   c.flags[1] = upd;
   if (c.use_graph_cond) {

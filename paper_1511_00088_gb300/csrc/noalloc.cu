@@ -25,7 +25,7 @@
 #include "stag.h"
 
 namespace stag {
-int ctx_fp64_links(const stag_ctx *c, const void **links, Geom *g, cudaStream_t *stream, int *device);
+int ctx_fp64_links(const stag_ctx *c, const void **links, cudaStream_t *stream);
 void ctx_set_error(stag_ctx *c, const char *msg);
 Geom ctx_geom(const stag_ctx *c);
 int ctx_device(const stag_ctx *c);
@@ -167,13 +167,15 @@ __global__ void __launch_bounds__(NA_BT) k_na_deo_dot(const Geom g, const void *
   }
 }
 
-bool na_is_device(const void *p) {
+// p is device memory of `device` (or managed memory, which every device reaches)
+bool na_is_device(const void *p, int device) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 }  // namespace
@@ -197,16 +199,15 @@ extern "C" int stag_mdagm_dot_noalloc(stag_ctx *ctx, double mass, const double *
     ctx_set_error(ctx, "stag_mdagm_dot_noalloc: cudaSetDevice failed");
     return STAG_ERR_CUDA;
   }
-  if (!na_is_device(in_even) || !na_is_device(tmp_odd) || !na_is_device(out_even) ||
-      (dot && !na_is_device(dot))) {
-    ctx_set_error(ctx, "stag_mdagm_dot_noalloc: every pointer must be device memory");
+  const int dev = ctx_device(ctx);
+  if (!na_is_device(in_even, dev) || !na_is_device(tmp_odd, dev) || !na_is_device(out_even, dev) ||
+      (dot && !na_is_device(dot, dev))) {
+    ctx_set_error(ctx, "stag_mdagm_dot_noalloc: every pointer must be device memory of the context's GPU");
     return STAG_ERR_ARG;
   }
   const void *links = nullptr;
-  Geom gg;
   cudaStream_t st;
-  int dev;
-  if (ctx_fp64_links(ctx, &links, &gg, &st, &dev) != STAG_OK) {
+  if (ctx_fp64_links(ctx, &links, &st) != STAG_OK) {
     ctx_set_error(ctx, "no gauge field: call stag_links_upload first");
     return STAG_ERR_STATE;
   }

@@ -149,6 +149,9 @@ struct DsArgs {
   // memory (bulk copies), 2 straight into registers
   int tma, ntile;
   const void *links_tile;
+  // tma == 1 only: 1 makes every bounded wait for staged links give up at once
+  // (the failure path run on purpose: flag, drain, STAG_ERR_TIMEOUT)
+  int wait_giveup;
   // host side only (launch attribute): l2_bytes > 0 marks [l2_base, l2_base +
   // l2_bytes) as an L2 access-policy window, a fraction l2_hit of it persisting
   const void *l2_base;
@@ -363,11 +366,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // wait until the phase with parity `parity` of the barrier has completed;
 // gives up (false) after about a second (the global timer, checked every 64
-// polls) or 2^20 polls, whichever comes first
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// polls) or max_polls polls, whichever comes first (max_polls = 0: gives up
+// at once unless nothing is awaited)
+constexpr int MBAR_MAX_POLLS = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int max_polls = MBAR_MAX_POLLS) {
   const uint32_t b = smem_addr(bar);
   const unsigned long long t0 = global_ns();
-  for (int i = 0; i < (1 << 20); ++i) {
+  for (int i = 0; i < max_polls; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -799,13 +804,22 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
   constexpr unsigned CHUNK = (unsigned)(SPB * 8 * NEL * sizeof(LS2));
   extern __shared__ __align__(128) unsigned char stage_mem[];
   __shared__ __align__(8) uint64_t stage_bar[NSTG];
-  __shared__ volatile int stage_failed;  // a bounded wait of this block gave up
+  // a bounded wait of this block gave up, or an earlier kernel's did: no more
+  // copies are issued and no thread waits again (the results are void)
+  __shared__ volatile int stage_failed;
   const int nmine = bx0 < nchunk ? (nchunk - 1 - bx0) / nbx + 1 : 0;  // chunks of this block
+  // Chunk q goes to stage q % NSTG, whose barrier completes phase q / NSTG when
+  // it lands.  Chunk q + NSTG is issued only after every thread has waited for
+  // chunk q successfully, so each stage has at most one copy outstanding: that
+  // of the last chunk issued into it.  `issued` (thread 0) counts the chunks.
+  int issued = 0;
   auto issue = [&](int q) {  // bulk copy of this block's chunk q into stage q % NSTG
     const LS2 *src = reinterpret_cast<const LS2 *>(a.links_tile) +
                      ((long long)a.par_out * a.ntile + (long long)(bx0 + q * nbx) * (SPB / LT)) * (8 * NEL * LT);
     bulk_copy_g2s(stage_mem + (q % NSTG) * CHUNK, src, CHUNK, &stage_bar[q % NSTG]);
+    issued = q + 1;
   };
+  const int wait_polls = a.wait_giveup ? 0 : MBAR_MAX_POLLS;
   if (TMA == 1) {
     if (threadIdx.x == 0) {
       for (int q = 0; q < NSTG; ++q) mbar_init(&stage_bar[q], 1);
@@ -817,6 +831,11 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
       for (int q = 0; q < NSTG - 1 && q < nmine; ++q) issue(q);
   }
   grid_dep_wait();
+  if (TMA == 1) {
+    // an earlier kernel of this solve gave up: this one waits for nothing
+    if (threadIdx.x == 0 && a.ctl.flags != nullptr && *(volatile int *)(a.ctl.flags + 4) != 0) stage_failed = 1;
+    __syncthreads();
+  }
   // the systems' states: as stored, or advanced past the previous kernel's
   // reduction by this block (fold)
   __shared__ SysState sst[NS];
@@ -850,11 +869,11 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
   const LS2 *lsm = nullptr;  // this round's links in shared memory (TMA == 1)
   if (TMA == 1) {
     if (round > 0) __syncthreads();  // every thread is done with the stage read last round
-    if (threadIdx.x == 0 && round + NSTG - 1 < nmine) {
+    if (threadIdx.x == 0 && !stage_failed && round + NSTG - 1 < nmine) {
       fence_proxy_async_smem();
       issue(round + NSTG - 1);
     }
-    if (!stage_failed && !mbar_wait(&stage_bar[round % NSTG], (unsigned)(round / NSTG) & 1u)) {
+    if (!stage_failed && !mbar_wait(&stage_bar[round % NSTG], (unsigned)(round / NSTG) & 1u, wait_polls)) {
       stage_failed = 1;  // this block waits no more; the host reports the error
       if (a.ctl.flags != nullptr) atomicExch(a.ctl.flags + 4, 1);
     }
@@ -1137,10 +1156,12 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
   if (TMA == 1) {
     __syncthreads();  // every thread's stage_failed visible: the branch below is uniform
     if (stage_failed) {
-      // copies that may still be in flight land before the block exits
-      // (bounded again; the results of this launch are void in any case)
+      // the copy still outstanding in each stage (that of the last chunk
+      // issued into it) lands before the block exits: a wait on its phase,
+      // bounded again (the results of this launch are void in any case)
       if (threadIdx.x == 0)
-        for (int q = 0; q < NSTG; ++q) mbar_wait(&stage_bar[q], 0u), mbar_wait(&stage_bar[q], 1u);
+        for (int q = issued - NSTG > 0 ? issued - NSTG : 0; q < issued; ++q)
+          mbar_wait(&stage_bar[q % NSTG], (unsigned)(q / NSTG) & 1u);
       __syncthreads();
     }
   }

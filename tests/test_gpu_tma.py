@@ -76,3 +76,43 @@ def test_tiled_half_links(prec, path):
     x1, it1, tr1 = solve_with(L, U, b, m, prec, False, path, 2)
     t = oracle.true_residual(L, U, m, b, x1)
     assert t <= 1e-10 and abs(t - tr1) <= 1e-12 + 0.05 * t
+
+
+@pytest.mark.parametrize("eager", [False, True])
+def test_wait_giveup_reports_timeout_promptly(eager):
+    """The bounded wait of the shared-memory link path, made to give up at once
+    (STAG_TEST_WAIT_GIVEUP=1): the solve stops after the pass in which it gave
+    up, returns STAG_ERR_TIMEOUT ("void") within seconds, every bulk copy has
+    landed before its block exits, and the GPU context stays usable."""
+    import time
+    L = (6, 6, 6, 12)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 91)
+    b = synth.gaussian_vector(V // 2, 92)
+    keys = ("STAG_TMA", "STAG_LANES", "STAG_TEST_WAIT_GIVEUP", "STAG_EAGER")
+    old = {k: os.environ.get(k) for k in keys}
+    os.environ.update({"STAG_TMA": "1", "STAG_LANES": "1", "STAG_TEST_WAIT_GIVEUP": "1",
+                       "STAG_EAGER": "1" if eager else "0"})
+    try:
+        with stag.Context(L) as ctx:
+            ctx.links_upload(U)
+            bt = torch.from_numpy(b).cuda()
+            xt = torch.empty_like(bt)
+            t0 = time.perf_counter()
+            st, it, tr = stag.stag_cg_solve(ctx.h, [bt], [0.05], 1e-10, 20000, stag.STAG_FP32, [xt])
+            dt = time.perf_counter() - t0
+            assert st == stag.STAG_ERR_TIMEOUT, stag.status_name(st)
+            assert "void" in stag.stag_last_error(ctx.h)
+            assert dt < 10.0, dt
+            passes, _ = ctx.solve_counters()
+            assert passes <= 8, passes  # the loop ended right after the give-up
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    torch.cuda.synchronize()
+    # the same link path without the forced give-up still solves
+    x, it, tr = solve_with(L, U, b, 0.05, stag.STAG_FP32, False, 1, 1)
+    assert oracle.true_residual(L, U, 0.05, b, x) <= 1e-10

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1511_00088_gb300 import stag, synth
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +51,14 @@ def test_noalloc_matches_allocating_entry_points_on_two_calls():
             assert rel(t, ref_t) <= 1e-13
             d_ref = torch.vdot(x.flatten(), ref.flatten()).real.item()
             assert abs(dot.item() - d_ref) <= 1e-12 * abs(d_ref)
+            # and against the FP64 CPU oracle directly: A x, D_oe x and <x, A x>
+            xh = x.cpu().numpy()
+            o_ref = oracle.mdagm(L, U, m, xh)
+            t_ref = oracle.dslash_oe(L, U, xh)
+            assert np.linalg.norm(out.cpu().numpy() - o_ref) <= 1e-13 * np.linalg.norm(o_ref)
+            assert np.linalg.norm(t.cpu().numpy() - t_ref) <= 1e-13 * np.linalg.norm(t_ref)
+            d_orc = float(np.vdot(xh.reshape(-1), o_ref.reshape(-1)).real)
+            assert abs(dot.item() - d_orc) <= 1e-12 * abs(d_orc)
 
 
 def test_noalloc_rejects_oversized_lattice_and_host_pointers():
