@@ -68,6 +68,17 @@ extern "C" {
  * are stored at FP16/BF16 and the Krylov vectors stay FP32. */
 #define STAG_HALF_VECTORS 0x200
 
+/* OR-ed into the precision of stag_cg_solve / stag_time_cg_kernel with
+ * STAG_FP32 links (or links of the same half format): store the Krylov
+ * vectors p and D_oe p at FP16 / BF16 with a per-site FP32 scale (value =
+ * code x scale, scale = max |component| of the site), independently of the
+ * links.  The iterated residual and the partial solution stay FP32, the
+ * arithmetic FP32, the reliable updates FP64.  Links rounded to FP16/BF16
+ * change A itself; rounded vectors only perturb each A p, by D_eo applied to
+ * the rounding of D_oe p. */
+#define STAG_VEC_FP16 0x400
+#define STAG_VEC_BF16 0x800
+
 /* context flags */
 #define STAG_ANTIPERIODIC_T 1 /* antiperiodic boundary in t (the sign b_mu above) */
 #define STAG_RECON12 2 /* reduced-precision links keep rows 0,1; row 2 = conj(row0 x row1) */
@@ -126,7 +137,7 @@ int stag_mdagm(stag_ctx *ctx, int precision, double mass, const double *in_even,
  *   precision  STAG_FP64: plain FP64 CG.  STAG_FP32/FP16/BF16: the inner
  *              iteration runs with links stored at that precision (FP32
  *              arithmetic; Krylov vectors FP32, or FP16/BF16 per-site scaled
- *              with STAG_HALF_VECTORS), the
+ *              with STAG_VEC_FP16 / STAG_VEC_BF16 / STAG_HALF_VECTORS), the
  *              solution is accumulated and the residual recomputed in FP64
  *              whenever the iterated residual has dropped by 10x since the last
  *              recomputation ("reliable update"), and at convergence.
@@ -145,6 +156,27 @@ int stag_mdagm(stag_ctx *ctx, int precision, double mass, const double *in_even,
 int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const double masses[],
                   int nmass, double tol, int maxiter, int precision, double *const x[],
                   int iters[], double true_res[]);
+
+/*
+ * Solve the full-lattice staggered equation M x = b, M = 2m + D (the operator
+ * at the top of this header with its mass term; Sec. 3 of the paper: the
+ * equation the CG inverter serves, its even-site Schur complement being what
+ * stag_cg_solve inverts), for every source and mass, by the even-odd route:
+ *   b_s = 2m b_e - D_eo b_o                     (FP64, on the GPU),
+ *   (4 m^2 - D_eo D_oe) x_e = b_s               (the CG of stag_cg_solve),
+ *   x_o = (b_o - D_oe x_e) / (2m)               (FP64, on the GPU).
+ *   src[r], x[r * nmass + k]  full-lattice vectors [V][3][2] FP64 in the
+ *              lexicographic site order of the links, host or device;
+ *   masses     finite and > 0;
+ *   tol        stop when ||b - M x|| / ||b|| <= tol: with x_o as above the odd
+ *              rows of b - M x vanish (to rounding) and the even rows are
+ *              (b_s - A x_e) / (2m), so the CG holds its FP64 residual to
+ *              ||b_s - A x_e|| <= tol 2m ||b||;
+ *   true_res[] (may be NULL) ||b_s - A x_e|| / (2m ||b||), recomputed in FP64.
+ * precision, maxiter, iters[] and the statuses as in stag_cg_solve.
+ */
+int stag_solve_full(stag_ctx *ctx, const double *const src[], int nrhs, const double masses[], int nmass,
+                    double tol, int maxiter, int precision, double *const x[], int iters[], double true_res[]);
 
 /*
  * Average device time of one launch of one of the two half-operator kernels
@@ -264,6 +296,30 @@ int stag_mdagm_dot_noalloc(stag_ctx *ctx, double mass, const double *in_even, do
  * Host or device pointers.  Errors: STAG_ERR_ARG, STAG_ERR_STATE, _CUDA.
  */
 int stag_force(stag_ctx *ctx, const double *x_even, double *grad_links, double *lie_force);
+
+/*
+ * The fermion action S = phi^dag A^{-1} phi (A = 4 m^2 - D_eo D_oe; the
+ * molecular-dynamics action of the staggered quarks whose inverter is Sec. 3's
+ * CG) at an approximate solution x of A x = phi, in the stationary form
+ *   S = 2 Re<phi, x> - Re<x, A x>,
+ * exact at the exact solution and with an error second order in the residual
+ * phi - A x (Re<phi, x> alone is first order).  A x in FP64; every site's term
+ * summed in double-word (two-sum) FP64 arithmetic in a fixed order, so S
+ * carries a few units of FP64 rounding and repeats bit for bit.  phi_even and
+ * x_even are [Ve][3][2] FP64, host or device; *S is host memory.
+ * Errors: STAG_ERR_ARG, STAG_ERR_STATE, STAG_ERR_CUDA.
+ */
+int stag_action(stag_ctx *ctx, double mass, const double *phi_even, const double *x_even, double *S);
+
+/*
+ * Backward pass of the action for an autograd engine: given x_even = A^{-1}
+ * phi and the upstream factor gS = dL/dS,
+ *   grad_links [4][V][3][3][2] (may be NULL) = gS K^dag (as stag_force),
+ *   grad_phi   [Ve][3][2]      (may be NULL) = 2 gS x  (dS/dphi in the torch
+ *              convention dS/dRe phi + i dS/dIm phi, S being real).
+ * Host or device pointers.  Errors: STAG_ERR_ARG, STAG_ERR_STATE, _CUDA.
+ */
+int stag_action_backward(stag_ctx *ctx, const double *x_even, double gS, double *grad_links, double *grad_phi);
 
 /* Message of the last error on this context ("" when none). */
 const char *stag_last_error(const stag_ctx *ctx);

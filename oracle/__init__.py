@@ -31,18 +31,22 @@ _LIB = os.path.join(_HERE, "libstag_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
+_LIB_OMP = os.path.join(_HERE, "libstag_oracle_omp.so")
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (once; again when the source is newer)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (once; again when the source is newer).
+    openmp=True builds the all-core timing copy (the per-site loop of the
+    operator in parallel, results bit-identical to the serial build)."""
+    lib = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, lib)
+    return lib
 
 
 def _bind(path):
@@ -67,6 +71,8 @@ def _bind(path):
         "orc_round_links": (None, [I, L, P, P]),
         "orc_force_K": (None, [P, I, P, P, P]),
         "orc_force_lie": (None, [L, P, P, P]),
+        "orc_set_threads": (None, [I]),
+        "orc_threads": (I, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -88,6 +94,37 @@ class using:
         self.saved = _lib
         _lib = _bind(self.path)
         return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+class threads:
+    """Context manager: route this module's functions to the all-core build of
+    the oracle with n threads (n = 0: every core).  Results are bit-identical
+    to the serial build; only the operator's per-site loop runs in parallel.
+    If the compiler cannot build it, the serial build stays in use."""
+
+    def __init__(self, n=0):
+        self.n = int(n) if n else (os.cpu_count() or 1)
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        try:
+            lib = _bind(build(openmp=True))
+            lib.orc_set_threads(self.n)
+            _lib = lib
+        except (OSError, subprocess.CalledProcessError):
+            pass
+        return self
+
+    def count(self):
+        """Threads the routed library actually uses."""
+        return int(_load().orc_threads())
 
     def __exit__(self, *exc):
         global _lib

@@ -1,11 +1,13 @@
 """Differentiable staggered fermion action S = phi^dag (M^dag M)^{-1} phi.
 
 The forward pass solves (4 m^2 - D_eo D_oe) X = phi with the library's CG and
-returns S = Re <phi, X>.  The backward pass is hand-written: one half operator
-Y = D_oe X and one pass over the links (stag_force) give the gauge-field
-gradient in the torch convention dS/dRe U + i dS/dIm U; the source gradient is
-2 X.  X is kept from the forward pass, so the backward needs no further solve.
-All arithmetic runs in libstag (CUDA); this module only marshals tensors.
+evaluates S in the library (stag_action: the stationary form 2 Re<phi, X> -
+Re<X, A X>, double-word FP64 sums on the GPU).  The backward pass is
+hand-written in the library too (stag_action_backward): one half operator
+Y = D_oe X and one pass over the links give gS times the gauge-field gradient
+dS/dRe U + i dS/dIm U, and the source gradient 2 gS X.  X is kept from the
+forward pass, so the backward needs no further solve.  This module only
+allocates and marshals tensors.
 """
 from __future__ import annotations
 
@@ -22,22 +24,23 @@ class FermionAction(torch.autograd.Function):
         if not (links.is_cuda and phi.is_cuda):
             raise ValueError("links and phi must be CUDA tensors (complex128)")
         context.links_upload(links.detach().contiguous())
-        xs, st, it, tr = context.cg_solve([phi.detach().contiguous()], [mass], tol=tol, maxiter=maxiter,
-                                          precision=precision)
+        phi_c = phi.detach().contiguous()
+        xs, st, it, tr = context.cg_solve([phi_c], [mass], tol=tol, maxiter=maxiter, precision=precision)
         X = xs[0]
+        S = context.action(phi_c, X, mass)
         fctx.save_for_backward(X)
         fctx.context = context
-        return torch.real(torch.vdot(phi.reshape(-1), X.reshape(-1)))
+        return torch.tensor(S, dtype=torch.float64, device=phi.device)
 
     @staticmethod
     def backward(fctx, gS):
         (X,) = fctx.saved_tensors
-        grad_links = grad_phi = None
-        if fctx.needs_input_grad[0]:
-            G, _ = fctx.context.force(X, grad=True, lie=False)
-            grad_links = gS * G
-        if fctx.needs_input_grad[1]:
-            grad_phi = 2.0 * gS * X
+        g = float(gS)
+        grad_links = torch.empty((4, fctx.context.V, 3, 3), dtype=torch.complex128, device=X.device) \
+            if fctx.needs_input_grad[0] else None
+        grad_phi = torch.empty_like(X) if fctx.needs_input_grad[1] else None
+        if grad_links is not None or grad_phi is not None:
+            fctx.context.action_backward(X, g, grad_links, grad_phi)
         return grad_links, grad_phi, None, None, None, None, None
 
 

@@ -196,6 +196,8 @@ struct stag_ctx {
   bool tile_ok[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
   DevBuf stage_in, stage_out;  // FP64 ABI-layout vectors for host transfers
   VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
+  VecBuf full_e, full_o, full_x;  // full-lattice solve: halves of the sources, odd half of a solution
+  DevBuf red;                     // block sums of the action's reduction
   DevBuf defect;
   Work w;
   int last_nsys = 0;  // systems of the most recent solve (stats in w.h_st)
@@ -232,15 +234,28 @@ int arg_err(stag_ctx *c, const char *msg) {
 
 int valid_prec(int p) { return p == P64 || p == P32 || p == P16 || p == PBF; }
 
-// Solver precision argument: link storage in the low byte; STAG_HALF_VECTORS
-// also stores the Krylov vectors at FP16/BF16 (per-site scaled).
+// Solver precision argument: link storage in the low byte; the Krylov vectors
+// p and t at FP32, or at FP16/BF16 (per-site scaled) with STAG_VEC_FP16 /
+// STAG_VEC_BF16 (any reduced-precision links) or STAG_HALF_VECTORS (the
+// links' own FP16/BF16).  The residual and the partial solution stay FP32.
 bool solver_precs(int precision, int *LP, int *VP, int *RP) {
   const int P = precision & 0xff;
-  const bool hv = (precision & STAG_HALF_VECTORS) != 0;
-  if (!valid_prec(P) || (precision & ~(0xff | STAG_HALF_VECTORS))) return false;
-  if (hv && !(P == P16 || P == PBF)) return false;
+  const int vbits = precision & (STAG_HALF_VECTORS | STAG_VEC_FP16 | STAG_VEC_BF16);
+  if (!valid_prec(P) || (precision & ~(0xff | STAG_HALF_VECTORS | STAG_VEC_FP16 | STAG_VEC_BF16))) return false;
+  int vp = (P == P64) ? P64 : P32;
+  if (vbits == STAG_HALF_VECTORS) {
+    if (!(P == P16 || P == PBF)) return false;
+    vp = P;
+  } else if (vbits == STAG_VEC_FP16 || vbits == STAG_VEC_BF16) {
+    const int want = (vbits == STAG_VEC_FP16) ? P16 : PBF;
+    // FP32 links with either; half links with vectors of their own format
+    if (!(P == P32 || P == want)) return false;
+    vp = want;
+  } else if (vbits != 0) {
+    return false;  // more than one vector format
+  }
   *LP = P;
-  *VP = (P == P64) ? P64 : (hv ? P : P32);
+  *VP = vp;
   *RP = (P == P64) ? P64 : P32;
   return true;
 }
@@ -1135,7 +1150,16 @@ int build_graph_inner(stag_ctx *c) {
   return STAG_OK;
 }
 
-// Solve phases (shared by the single and the ragged solve)
+// Solve phases (shared by the single, the ragged and the full-lattice solve)
+// start: per-system parameters and the CG start, on c->stream, with the
+// sources already in w.b64.  full != nullptr (a full-lattice solve): the even
+// and odd halves of the full sources, whose (2m)^2 |b|^2 becomes each
+// system's reference norm.
+struct FullRef {
+  VecArg be, bo;
+};
+int solve_start(stag_ctx *c, const double masses[], int nmass, double tol, int maxiter, const FullRef *full);
+
 // stage: sources, per-system parameters and the CG start, on c->stream
 int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass, double tol,
                 int maxiter, int prec) {
@@ -1150,6 +1174,12 @@ int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double m
     CKS(vec_in(c, src[r], c->stage_in, 0, &d));
     for (int k = 0; k < nmass; ++k) CK(launch_pack_vec(P64, d, w.b64.arg(), r * nmass + k, c->Ve, c->stream));
   }
+  return solve_start(c, masses, nmass, tol, maxiter, nullptr);
+}
+
+int solve_start(stag_ctx *c, const double masses[], int nmass, double tol, int maxiter, const FullRef *full) {
+  Work &w = c->w;
+  const int nsys = w.nsys;
   // per-system parameters
   SysState *hs = (SysState *)w.h_st.p;
   CK(cudaStreamSynchronize(c->stream));  // pinned staging buffer reuse
@@ -1160,6 +1190,7 @@ int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double m
     hs[j].tol = tol;
     hs[j].delta = (w.prec == P64) ? 0.0 : 0.1;
     hs[j].maxiter = maxiter;
+    hs[j].ref_full = full ? 1 : 0;
   }
   CK(cudaMemcpyAsync(w.st.p, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, c->stream));
   {
@@ -1177,6 +1208,11 @@ int solve_stage(stag_ctx *c, const double *const src[], int nrhs, const double m
     BlasArgs b = blas_base(c, ctl0);
     b.gate = GATE_NONE;
     b.fin = FIN_INIT;
+    if (full) {
+      b.be = full->be;
+      b.bo = full->bo;
+      b.ref_nmass = nmass;
+    }
     CK(launch_cg_init(w.VP, w.RP, w.NS, w.nbx_bl * w.G, c->stream, b));
     CK(launch_finalize(ctl0, FIN_INIT, w.nbx_bl, 2, nsys, c->stream));
   }
@@ -1202,15 +1238,25 @@ int solve_eager(stag_ctx *c, int maxiter) {
   return STAG_OK;
 }
 
+int solve_status(stag_ctx *c, int iters[], double true_res[]);
+
 // copy the solutions and statistics out; the solve's status
 int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[]) {
   Work &w = c->w;
   const int nsys = w.nsys;
+  CK(cudaMemcpyAsync(w.h_st.p, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
+  for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
+  return solve_status(c, iters, true_res);
+}
+
+// after the states and flags were queued for the host: wait, release the L2
+// set-aside, and the solve's status with per-system iterations and residuals
+int solve_status(stag_ctx *c, int iters[], double true_res[]) {
+  Work &w = c->w;
+  const int nsys = w.nsys;
   SysState *hs = (SysState *)w.h_st.p;
   int *hf = (int *)w.h_flags.p;
-  CK(cudaMemcpyAsync(hs, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(hf, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
-  for (int j = 0; j < nsys; ++j) CKS(vec_out(c, w.x64, j, x[j]));
   CK(cudaStreamSynchronize(c->stream));
   c->last_nsys = nsys;
   // the solve's persisting L2 lines back to normal (the next user of L2, or a
@@ -1236,9 +1282,17 @@ int solve_finish(stag_ctx *c, double *const x[], int iters[], double true_res[])
   return status;
 }
 
+int solve_run(stag_ctx *c, int maxiter);
+
 int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
                double tol, int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
   CKS(solve_stage(c, src, nrhs, masses, nmass, tol, maxiter, prec));
+  CKS(solve_run(c, maxiter));
+  return solve_finish(c, x, iters, true_res);
+}
+
+// run the staged solve: one graph launch, or eager launches without graphs
+int solve_run(stag_ctx *c, int maxiter) {
   Work &w = c->w;
   bool ran = false;
   if (c->use_graph) {
@@ -1261,7 +1315,95 @@ int solve_impl(stag_ctx *c, const double *const src[], int nrhs, const double ma
     if (w.l2p) l2_setaside(c, true);
     CKS(solve_eager(c, maxiter));
   }
-  return solve_finish(c, x, iters, true_res);
+  return STAG_OK;
+}
+
+// One FP64 half operator with the mass epilogue on system slots of FP64
+// vectors: out[ko] = scale (m4 center[kc] - D in[ki]) on the sites of parity
+// par_out (scale = 0: no scaling).  The vectors are views of one system each.
+VecArg vec_slot(const VecBuf &v, int k) {
+  VecArg a = v.arg();
+  a.v = (char *)a.v + cplx_bytes(v.prec) * (size_t)a.sstr * k;
+  return a;
+}
+
+int apply_m64(stag_ctx *c, int par_out, double m4, double scale, VecArg in, VecArg center, VecArg out) {
+  int lanes = 1;
+  CKS(tune_lanes(c, P64, 0, P64, 1, 1, 1, c->links64.p, in, out, &lanes));
+  DsArgs a = ds_base(c);
+  a.links = c->links64.p;
+  a.nsys = 1;
+  a.ngroups = 1;
+  a.ctl = no_ctl();
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.m4_single = m4;
+  a.out_scale = scale;
+  a.par_out = par_out;
+  a.in = in;
+  a.center = center;
+  a.out = out;
+  CK(launch_dslash(P64, 0, P64, P64, 1, EPI_MDAGM, lanes, ds_blocks(c->Ve, lanes), c->stream, a));
+  return STAG_OK;
+}
+
+// The full-lattice equation M x = b, M = 2m + D, through the even-site CG:
+//   b_s = 2m b_e - D_eo b_o;  (4m^2 - D_eo D_oe) x_e = b_s;  x_o = (b_o - D_oe x_e) / (2m)
+// (all FP64 except the CG's inner iteration).  The CG's reference norm is
+// 2m |b|: with x_o as above the odd rows of b - M x vanish (to rounding) and
+// the even rows are (b_s - A x_e) / (2m), so |b - M x| / |b| = |r_s| / (2m |b|).
+int solve_full_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+                    double tol, int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
+  const int nsys = nrhs * nmass;
+  CKS(work_prepare(c, nsys, prec));
+  Work &w = c->w;
+  const void *lo = nullptr;
+  CKS(links_for(c, w.prec, &lo));
+  const int Ve = c->Ve;
+  const size_t full_bytes = sizeof(double) * 6ull * (size_t)c->V;
+  CK(c->full_e.ensure(P64, nrhs, Ve));
+  CK(c->full_o.ensure(P64, nrhs, Ve));
+  CK(c->full_x.ensure(P64, 1, Ve));
+  // full sources -> their even and odd halves
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *d = nullptr;
+    if (is_device_ptr(src[r])) {
+      d = reinterpret_cast<const double2 *>(src[r]);
+    } else {
+      CK(c->stage_in.ensure(full_bytes));
+      CK(cudaMemcpyAsync(c->stage_in.p, src[r], full_bytes, cudaMemcpyHostToDevice, c->stream));
+      d = reinterpret_cast<const double2 *>(c->stage_in.p);
+    }
+    CK(launch_split_full(d, c->full_e.arg(), c->full_o.arg(), r, c->g, c->stream));
+  }
+  // even-site sources b_s = 2m b_e - D_eo b_o of every system
+  for (int r = 0; r < nrhs; ++r)
+    for (int k = 0; k < nmass; ++k)
+      CKS(apply_m64(c, 0, 2.0 * masses[k], 0.0, vec_slot(c->full_o, r), vec_slot(c->full_e, r),
+                    vec_slot(w.b64, r * nmass + k)));
+  FullRef ref;
+  ref.be = c->full_e.arg();
+  ref.bo = c->full_o.arg();
+  CKS(solve_start(c, masses, nmass, tol, maxiter, &ref));
+  CKS(solve_run(c, maxiter));
+  CK(cudaMemcpyAsync(w.h_st.p, w.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
+  // x_o = (b_o - D_oe x_e) / (2m), then both halves into the caller's full vector
+  for (int j = 0; j < nsys; ++j) {
+    const int r = j / nmass, k = j % nmass;
+    CKS(apply_m64(c, 1, 1.0, 1.0 / (2.0 * masses[k]), vec_slot(w.x64, j), vec_slot(c->full_o, r),
+                  c->full_x.arg()));
+    if (is_device_ptr(x[j])) {
+      CK(launch_merge_full(w.x64.arg(), j, c->full_x.arg(), 0, reinterpret_cast<double2 *>(x[j]), c->g,
+                           c->stream));
+    } else {
+      CK(c->stage_out.ensure(full_bytes));
+      CK(launch_merge_full(w.x64.arg(), j, c->full_x.arg(), 0, reinterpret_cast<double2 *>(c->stage_out.p), c->g,
+                           c->stream));
+      CK(cudaMemcpyAsync(x[j], c->stage_out.p, full_bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  return solve_status(c, iters, true_res);
 }
 
 // operator calls of the ABI: the FP64 input is rounded to `prec` (per-site
@@ -1319,6 +1461,79 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
     CK(launch_dslash(P, recon, VP, VP, 1, EPI_MDAGM, lanes, nb, c->stream, a));
   }
   CKS(vec_out(c, c->api_b, 0, out));
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
+}
+
+// out = D in (FP64) on the sites of parity par_out, one system
+int apply_m64_plain(stag_ctx *c, int par_out, VecArg in, VecArg out) {
+  int lanes = 1;
+  CKS(tune_lanes(c, P64, 0, P64, 1, 1, 1, c->links64.p, in, out, &lanes));
+  DsArgs a = ds_base(c);
+  a.links = c->links64.p;
+  a.nsys = 1;
+  a.ngroups = 1;
+  a.ctl = no_ctl();
+  a.gate = GATE_NONE;
+  a.fin = FIN_NONE;
+  a.par_out = par_out;
+  a.in = in;
+  a.out = out;
+  CK(launch_dslash(P64, 0, P64, P64, 1, EPI_PLAIN, lanes, ds_blocks(c->Ve, lanes), c->stream, a));
+  return STAG_OK;
+}
+
+// The fermion force at x_even, every output multiplied by `scale` (the
+// chain-rule factor of a caller): grad_links = scale K^dag, lie_force =
+// scale f_a, grad_phi = 2 scale x (each may be null; host or device).
+int force_impl(stag_ctx *c, const double *x_even, double scale, double *grad_links, double *lie_force,
+               double *grad_phi) {
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  const int Ve = c->Ve;
+  const double2 *d = nullptr;
+  CKS(vec_in(c, x_even, c->stage_in, 0, &d));
+  if (grad_phi) {
+    const size_t vb = sizeof(double) * 6ull * Ve;
+    if (is_device_ptr(grad_phi)) {
+      CK(launch_scale_reals((const double *)d, 2.0 * scale, grad_phi, 6ll * Ve, c->stream));
+    } else {
+      CK(c->stage_out.ensure(vb));
+      CK(launch_scale_reals((const double *)d, 2.0 * scale, (double *)c->stage_out.p, 6ll * Ve, c->stream));
+      CK(cudaMemcpyAsync(grad_phi, c->stage_out.p, vb, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));  // stage_out is reused below
+    }
+  }
+  if (!grad_links && !lie_force) {
+    CK(cudaStreamSynchronize(c->stream));
+    return STAG_OK;
+  }
+  CK(c->api_a.ensure(P64, 1, Ve));
+  CK(c->api_b.ensure(P64, 1, Ve));
+  CK(launch_pack_vec(P64, d, c->api_a.arg(), 0, Ve, c->stream));
+  // Y = D_oe X (FP64)
+  CKS(apply_m64_plain(c, 1, c->api_a.arg(), c->api_b.arg()));
+  const size_t gbytes = sizeof(double) * 18ull * 4ull * c->V, lbytes = sizeof(double) * 8ull * 4ull * c->V;
+  double2 *gdev = nullptr;
+  double *ldev = nullptr;
+  const bool g_host = grad_links && !is_device_ptr(grad_links);
+  const bool l_host = lie_force && !is_device_ptr(lie_force);
+  size_t off = 0;
+  if (g_host) off += gbytes;
+  if (l_host) off += lbytes;
+  if (off) CK(c->stage_out.ensure(off));
+  off = 0;
+  if (grad_links) {
+    gdev = g_host ? (double2 *)c->stage_out.p : (double2 *)grad_links;
+    if (g_host) off += gbytes;
+  }
+  if (lie_force) ldev = l_host ? (double *)((char *)c->stage_out.p + off) : lie_force;
+  CK(launch_force(c->g, (const double2 *)c->api_a.data.p, (const double2 *)c->api_b.data.p, c->links64.p, gdev, ldev,
+                  scale, c->stream));
+  if (g_host) CK(cudaMemcpyAsync(grad_links, gdev, gbytes, cudaMemcpyDeviceToHost, c->stream));
+  if (l_host) CK(cudaMemcpyAsync(lie_force, ldev, lbytes, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return STAG_OK;
 }
@@ -1626,7 +1841,8 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
   {
     int a_, b_, c_;
     if (!solver_precs(precision, &a_, &b_, &c_))
-      return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16 (FP16/BF16 optionally | STAG_HALF_VECTORS)");
+      return arg_err(c, "precision must be STAG_FP64/FP32/FP16/BF16, reduced precisions optionally | "
+                        "STAG_VEC_FP16 / STAG_VEC_BF16 (or FP16/BF16 | STAG_HALF_VECTORS)");
   }
   for (int r = 0; r < nrhs; ++r)
     if (!src[r]) return arg_err(c, "NULL source");
@@ -1636,6 +1852,32 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_solve_full(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+                    double tol, int maxiter, int precision, double *const x[], int iters[], double true_res[]) {
+  if (!c) return STAG_ERR_ARG;
+  if (!src || !masses || !x) return arg_err(c, "NULL argument");
+  if (nrhs < 1 || nmass < 1) return arg_err(c, "nrhs and nmass must be >= 1");
+  if ((long long)nrhs * nmass > 4096) return arg_err(c, "at most 4096 systems per solve");
+  if (!(tol > 0.0) || !(tol < 1.0)) return arg_err(c, "tol must be in (0, 1)");
+  if (maxiter < 1) return arg_err(c, "maxiter must be >= 1");
+  {
+    int a_, b_, c_;
+    if (!solver_precs(precision, &a_, &b_, &c_)) return arg_err(c, "bad solver precision");
+  }
+  for (int r = 0; r < nrhs; ++r)
+    if (!src[r]) return arg_err(c, "NULL source");
+  for (int j = 0; j < nrhs * nmass; ++j)
+    if (!x[j]) return arg_err(c, "NULL solution buffer");
+  for (int k = 0; k < nmass; ++k)
+    if (!(masses[k] > 0.0) || !std::isfinite(masses[k])) return arg_err(c, "masses must be finite and > 0");
+  CK(cudaSetDevice(c->device));
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  return solve_full_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
 }
 
 int stag_cg_solve_ragged(const stag_solve_desc *descs, int ndesc, double tol, int maxiter, int precision) {
@@ -1671,49 +1913,47 @@ int stag_force(stag_ctx *c, const double *x_even, double *grad_links, double *li
   if (!x_even) return arg_err(c, "NULL solution vector");
   if (!grad_links && !lie_force) return arg_err(c, "no output requested");
   CK(cudaSetDevice(c->device));
+  return force_impl(c, x_even, 1.0, grad_links, lie_force, nullptr);
+}
+
+int stag_action_backward(stag_ctx *c, const double *x_even, double gS, double *grad_links, double *grad_phi) {
+  if (!c) return STAG_ERR_ARG;
+  if (!x_even) return arg_err(c, "NULL solution vector");
+  if (!grad_links && !grad_phi) return arg_err(c, "no output requested");
+  if (!std::isfinite(gS)) return arg_err(c, "non-finite gS");
+  CK(cudaSetDevice(c->device));
+  return force_impl(c, x_even, gS, grad_links, nullptr, grad_phi);
+}
+
+int stag_action(stag_ctx *c, double mass, const double *phi_even, const double *x_even, double *S) {
+  if (!c) return STAG_ERR_ARG;
+  if (!phi_even || !x_even || !S) return arg_err(c, "NULL argument");
+  if (!std::isfinite(mass)) return arg_err(c, "non-finite mass");
+  CK(cudaSetDevice(c->device));
   if (!c->have_links) {
     c->err = "no gauge field: call stag_links_upload first";
     return STAG_ERR_STATE;
   }
   const int Ve = c->Ve;
-  const double2 *d = nullptr;
-  CKS(vec_in(c, x_even, c->stage_in, 0, &d));
+  const size_t vb = sizeof(double) * 6ull * Ve;
+  const double2 *dphi = nullptr, *dx = nullptr;
+  CK(c->stage_in.ensure(2 * vb));  // both host inputs share it: no regrowth between the two
+  CKS(vec_in(c, phi_even, c->stage_in, 0, &dphi));
+  CKS(vec_in(c, x_even, c->stage_in, vb, &dx));
   CK(c->api_a.ensure(P64, 1, Ve));
   CK(c->api_b.ensure(P64, 1, Ve));
-  CK(launch_pack_vec(P64, d, c->api_a.arg(), 0, Ve, c->stream));
-  // Y = D_oe X (FP64)
-  int lanes = 1;
-  CKS(tune_lanes(c, P64, 0, P64, 1, 1, 1, c->links64.p, c->api_a.arg(), c->api_b.arg(), &lanes));
-  DsArgs a = ds_base(c);
-  a.links = c->links64.p;
-  a.nsys = 1;
-  a.ngroups = 1;
-  a.ctl = no_ctl();
-  a.gate = GATE_NONE;
-  a.fin = FIN_NONE;
-  a.par_out = 1;
-  a.in = c->api_a.arg();
-  a.out = c->api_b.arg();
-  CK(launch_dslash(P64, 0, P64, P64, 1, EPI_PLAIN, lanes, ds_blocks(Ve, lanes), c->stream, a));
-  const size_t gbytes = sizeof(double) * 18ull * 4ull * c->V, lbytes = sizeof(double) * 8ull * 4ull * c->V;
-  double2 *gdev = nullptr;
-  double *ldev = nullptr;
-  const bool g_host = grad_links && !is_device_ptr(grad_links);
-  const bool l_host = lie_force && !is_device_ptr(lie_force);
-  size_t off = 0;
-  if (g_host) off += gbytes;
-  if (l_host) off += lbytes;
-  if (off) CK(c->stage_out.ensure(off));
-  off = 0;
-  if (grad_links) {
-    gdev = g_host ? (double2 *)c->stage_out.p : (double2 *)grad_links;
-    if (g_host) off += gbytes;
-  }
-  if (lie_force) ldev = l_host ? (double *)((char *)c->stage_out.p + off) : lie_force;
-  CK(launch_force(c->g, (const double2 *)c->api_a.data.p, (const double2 *)c->api_b.data.p, c->links64.p, gdev, ldev,
-                  c->stream));
-  if (g_host) CK(cudaMemcpyAsync(grad_links, gdev, gbytes, cudaMemcpyDeviceToHost, c->stream));
-  if (l_host) CK(cudaMemcpyAsync(lie_force, ldev, lbytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(c->api_c.ensure(P64, 1, Ve));
+  CK(c->full_x.ensure(P64, 1, Ve));
+  CK(launch_pack_vec(P64, dx, c->api_a.arg(), 0, Ve, c->stream));
+  CK(launch_pack_vec(P64, dphi, c->full_x.arg(), 0, Ve, c->stream));
+  // t = D_oe x, A x = 4 m^2 x - D_eo t (FP64)
+  CKS(apply_m64_plain(c, 1, c->api_a.arg(), c->api_c.arg()));
+  CKS(apply_m64(c, 0, 4.0 * mass * mass, 0.0, c->api_c.arg(), c->api_a.arg(), c->api_b.arg()));
+  CK(c->red.ensure(sizeof(double) * (2ull * action_blocks(Ve) + 1)));
+  double *part = (double *)c->red.p;
+  double *dS = part + 2ll * action_blocks(Ve);
+  CK(launch_action(c->full_x.arg(), c->api_a.arg(), c->api_b.arg(), Ve, part, dS, c->stream));
+  CK(cudaMemcpyAsync(S, dS, sizeof(double), cudaMemcpyDefault, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return STAG_OK;
 }

@@ -152,6 +152,50 @@ cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve
   return cudaGetLastError();
 }
 
+__global__ void k_split_full(const double2 *__restrict__ full, VecArg e, VecArg o, int k, Geom g) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.Ve) return;
+#pragma unroll
+  for (int par = 0; par < 2; ++par) {
+    int x[4];
+    site_coords(g, par, s, x);
+    const long long lex = x[0] + (long long)g.L0 * (x[1] + (long long)g.L1 * (x[2] + (long long)g.L2 * x[3]));
+    double v[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 w = full[lex * 3 + c];
+      v[2 * c] = w.x;
+      v[2 * c + 1] = w.y;
+    }
+    store_vec<P64>(par == 0 ? e : o, k, s, g.Ve, v);
+  }
+}
+
+__global__ void k_merge_full(VecArg e, int ke, VecArg o, int ko, double2 *__restrict__ full, Geom g) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.Ve) return;
+#pragma unroll
+  for (int par = 0; par < 2; ++par) {
+    int x[4];
+    site_coords(g, par, s, x);
+    const long long lex = x[0] + (long long)g.L0 * (x[1] + (long long)g.L1 * (x[2] + (long long)g.L2 * x[3]));
+    double v[6];
+    load_vec_rw<P64>(par == 0 ? e : o, par == 0 ? ke : ko, s, g.Ve, v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) full[lex * 3 + c] = make_double2(v[2 * c], v[2 * c + 1]);
+  }
+}
+
+cudaError_t launch_split_full(const double2 *full, VecArg e, VecArg o, int k, Geom g, cudaStream_t st) {
+  k_split_full<<<nblk(g.Ve, 256), 256, 0, st>>>(full, e, o, k, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_full(VecArg e, int ke, VecArg o, int ko, double2 *full, Geom g, cudaStream_t st) {
+  k_merge_full<<<nblk(g.Ve, 256), 256, 0, st>>>(e, ke, o, ko, full, g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack_vec(int P, VecArg src, int k, double2 *dst, int Ve, cudaStream_t st) {
   const int nb = nblk(Ve, 256);
   switch (P) {

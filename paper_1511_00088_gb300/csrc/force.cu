@@ -15,7 +15,8 @@ namespace stag {
 
 // one thread per link (mu, lexicographic site); X, Y in the device SoA layout
 __global__ void k_force(const Geom g, const double2 *__restrict__ X, const double2 *__restrict__ Y,
-                        const void *links64, double2 *__restrict__ grad, double *__restrict__ lie) {
+                        const void *links64, double2 *__restrict__ grad, double *__restrict__ lie,
+                        double scale) {
   const long long V = 2ll * g.Ve;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 4 * V) return;
@@ -46,7 +47,7 @@ __global__ void k_force(const Geom g, const double2 *__restrict__ X, const doubl
   const double2 *A = par == 0 ? Y : X;
   const double2 *B = par == 0 ? X : Y;
   const int sa = sf, sbb = s;
-  const double c = par == 0 ? 2.0 * sg : -2.0 * sg;
+  const double c = (par == 0 ? 2.0 * sg : -2.0 * sg) * scale;  // scale: the caller's chain-rule factor
   double2 av[3], bv[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -100,9 +101,102 @@ __global__ void k_force(const Geom g, const double2 *__restrict__ X, const doubl
 }
 
 cudaError_t launch_force(Geom g, const double2 *X, const double2 *Y, const void *links64, double2 *grad,
-                         double *lie, cudaStream_t st) {
+                         double *lie, double scale, cudaStream_t st) {
   const long long n = 8ll * g.Ve;
-  k_force<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, X, Y, links64, grad, lie);
+  k_force<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, X, Y, links64, grad, lie, scale);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// the action S = phi^dag A^{-1} phi at an approximate solution x of A x = phi,
+// in the stationary form S = 2 Re<phi, x> - Re<x, A x> (its error is second
+// order in the residual phi - A x), summed in double-word arithmetic
+// ---------------------------------------------------------------------------
+// (hi, lo) += (bh, bl): Knuth's two-sum of the high parts (exact error term),
+// the low parts and that error added, then renormalised (fast two-sum).
+// Additions only, so no contraction into FMAs can change it.
+__device__ __forceinline__ void dw_add(double &hi, double &lo, double bh, double bl) {
+  const double s = hi + bh;
+  const double bb = s - hi;
+  const double e = (hi - (s - bb)) + (bh - bb);
+  const double t = (lo + bl) + e;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+
+__device__ __forceinline__ void dw_warp(double &hi, double &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
+    dw_add(hi, lo, h, l);
+  }
+}
+
+// fixed-order (hi, lo) sum over the block's threads -> thread 0
+template <int BT>
+__device__ __forceinline__ void dw_block(double &hi, double &lo) {
+  __shared__ double sh[BT / 32], sl[BT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  dw_warp(hi, lo);
+  if (lane == 0) {
+    sh[warp] = hi;
+    sl[warp] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < BT / 32; ++w) dw_add(hi, lo, sh[w], sl[w]);
+  }
+}
+
+constexpr int ACT_BT = 256;
+
+// per block: the double-word sum over its sites of 2 Re(phi . x) - Re(x . Ax)
+// (device SoA layout, one system) -> part[2 block], part[2 block + 1]
+__global__ void __launch_bounds__(ACT_BT) k_action_part(VecArg phi, VecArg x, VecArg ax, int Ve, double *part) {
+  const int s = blockIdx.x * ACT_BT + threadIdx.x;
+  double hi = 0.0, lo = 0.0;
+  if (s < Ve) {
+    double f[6], xv[6], av[6];
+    load_vec<P64>(phi, 0, s, Ve, f);
+    load_vec<P64>(x, 0, s, Ve, xv);
+    load_vec<P64>(ax, 0, s, Ve, av);
+    double d = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d += 2.0 * f[i] * xv[i] - xv[i] * av[i];
+    hi = d;
+  }
+  dw_block<ACT_BT>(hi, lo);
+  if (threadIdx.x == 0) {
+    part[2ll * blockIdx.x] = hi;
+    part[2ll * blockIdx.x + 1] = lo;
+  }
+}
+
+// one block: the nb block sums in a fixed order -> *out = hi + lo
+__global__ void __launch_bounds__(ACT_BT) k_action_sum(const double *part, int nb, double *out) {
+  double hi = 0.0, lo = 0.0;
+  for (int i = threadIdx.x; i < nb; i += ACT_BT) dw_add(hi, lo, part[2ll * i], part[2ll * i + 1]);
+  dw_block<ACT_BT>(hi, lo);
+  if (threadIdx.x == 0) *out = hi + lo;
+}
+
+// out = a x over n doubles (the source gradient 2 gS X of the action)
+__global__ void k_scale_reals(const double *__restrict__ x, double a, double *__restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i];
+}
+
+int action_blocks(int Ve) { return (Ve + ACT_BT - 1) / ACT_BT; }
+
+cudaError_t launch_action(VecArg phi, VecArg x, VecArg ax, int Ve, double *part, double *out, cudaStream_t st) {
+  const int nb = action_blocks(Ve);
+  k_action_part<<<nb, ACT_BT, 0, st>>>(phi, x, ax, Ve, part);
+  k_action_sum<<<1, ACT_BT, 0, st>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_reals(const double *x, double a, double *out, long long n, cudaStream_t st) {
+  k_scale_reals<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, a, out, n);
   return cudaGetLastError();
 }
 

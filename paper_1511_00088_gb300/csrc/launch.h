@@ -98,6 +98,9 @@ cudaError_t launch_finalize(const Ctl &c, int fin, int nbx, int nv, int nsys, cu
 cudaError_t launch_cg_init(int VP, int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 
 cudaError_t launch_pack_vec(int P, const double2 *src, VecArg dst, int k, int Ve, cudaStream_t st);
+// full-lattice ABI vector [V][3] -> system k of the even / odd halves (FP64), and back
+cudaError_t launch_split_full(const double2 *full, VecArg e, VecArg o, int k, Geom g, cudaStream_t st);
+cudaError_t launch_merge_full(VecArg e, int ke, VecArg o, int ko, double2 *full, Geom g, cudaStream_t st);
 cudaError_t launch_unpack_vec(int P, VecArg src, int k, double2 *dst, int Ve, cudaStream_t st);
 cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int nsys, int Ve,
                                cudaStream_t st);
@@ -112,6 +115,13 @@ cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long 
 // k_force over all 4 V links (force.cu): X even, Y = D_oe X odd (device SoA,
 // FP64); grad [4][V][3][3] complex and/or lie [4][V][8] (either may be null)
 cudaError_t launch_force(Geom g, const double2 *X, const double2 *Y, const void *links64, double2 *grad,
-                         double *lie, cudaStream_t st);
+                         double *lie, double scale, cudaStream_t st);
+// S = 2 Re<phi, x> - Re<x, ax> over Ve sites of one system (FP64 SoA), in
+// double-word arithmetic and a fixed order: part holds 2 action_blocks(Ve)
+// doubles of scratch, *out (device) receives S
+int action_blocks(int Ve);
+cudaError_t launch_action(VecArg phi, VecArg x, VecArg ax, int Ve, double *part, double *out, cudaStream_t st);
+// out[i] = a x[i], i < n (FP64)
+cudaError_t launch_scale_reals(const double *x, double a, double *out, long long n, cudaStream_t st);
 
 }  // namespace stag

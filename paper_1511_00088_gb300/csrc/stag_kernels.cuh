@@ -99,7 +99,8 @@ struct SysState {
                     // 2 iteration cap, -5 breakdown
   int update;       // a reliable update is pending (run at the end of the unrolled block)
   int n_updates;
-  int pad_;
+  int ref_full;     // 1: bnorm2 holds (2m)^2 |b|^2 of a full-lattice source b (the
+                    // even-site source b_s = 2m b_e - D_eo b_o is what the CG solves)
 };
 
 struct Ctl {
@@ -131,6 +132,7 @@ struct DsArgs {
   VecArg dir;            // EPI_RESID: the direction p at the residual's precision for
                          // Re<r, p> (v == nullptr: not reduced)
   double m4_single;      // 4 m^2 when ctl == nullptr
+  double out_scale;      // EPI_MDAGM: out = out_scale (m4 center - D in) when nonzero
   int nsys, ngroups;
   Ctl ctl;               // ctl.st == nullptr: no gating, no reductions
   int gate, fin;
@@ -165,6 +167,11 @@ struct BlasArgs {
   int nsys, ngroups;
   Ctl ctl;
   int gate, fin;
+  // k_cg_init of a full-lattice solve (be.v != nullptr): the even and odd
+  // halves of the full sources (FP64), source of system j = j / ref_nmass;
+  // the reference norm is (2m)^2 (|b_e|^2 + |b_o|^2) instead of |b|^2
+  VecArg be, bo;
+  int ref_nmass;
 };
 
 // ---------------------------------------------------------------------------
@@ -607,14 +614,14 @@ __device__ __forceinline__ void finalize_system(SysState &s, int fin, const doub
     s.bnorm2 = sum[0];
     s.rho = sum[1];
     s.rho_prev = sum[1];
-    s.rmax2 = sum[0];
+    s.rmax2 = s.ref_full ? sum[1] : sum[0];
     s.pnorm2 = 0.0;
     s.rp = 0.0;
     s.iter = 0;
     s.update = 0;
     s.n_updates = 0;
     s.alpha = s.beta = s.pAp = 0.0;
-    if (sum[0] == 0.0) {
+    if (sum[0] == 0.0 || (s.ref_full && sum[1] == 0.0)) {  // zero source (x = 0 is exact)
       s.true_res = 0.0;
       s.done = 1;
     } else {
@@ -1121,6 +1128,10 @@ __global__ void __launch_bounds__(BT, LP == P64 ? 4 : STAG_DS_MINB) k_dslash(con
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i) o[i] = m4[k] * cv[i] - acc[k][i];
+        if (a.out_scale != 0.0) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) o[i] *= (R)a.out_scale;
+        }
       } else {  // EPI_RESID (R = double)
         R xx[6], bv[6];
         R pv[6] = {0, 0, 0, 0, 0, 0};
@@ -1427,6 +1438,15 @@ __global__ void __launch_bounds__(BT) k_cg_init(const BlasArgs a) {
     store_vec<VP>(a.t, j, s, Ve, z);
     store_vec<RP>(a.x, j, s, Ve, z);
     store_vec<P64>(a.x64, j, s, Ve, z64);
+    if (a.be.v != nullptr) {  // full-lattice source: (2m)^2 |b_full|^2 at this site pair
+      double e[6], o[6];
+      load_vec<P64>(a.be, j / a.ref_nmass, s, Ve, e);
+      load_vec<P64>(a.bo, j / a.ref_nmass, s, Ve, o);
+      double q = 0.0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q += e[i] * e[i] + o[i] * o[i];
+      bb = a.ctl.st[j].m4 * q;
+    }
     part[k][0] = bb;
     part[k][1] = (double)rr;
   }
@@ -1465,6 +1485,12 @@ __global__ void k_unpack_vec(VecArg src, int k, double2 *__restrict__ dst, int V
 #pragma unroll
   for (int c = 0; c < 3; ++c) dst[(long long)s * 3 + c] = make_double2(v[2 * c], v[2 * c + 1]);
 }
+
+// full-lattice ABI vector [V][3] (lexicographic sites) <-> its even and odd
+// halves (system k of e / o, FP64 device layout); one thread per
+// checkerboard index s, which is one even and one odd site
+__global__ void k_split_full(const double2 *__restrict__ full, VecArg e, VecArg o, int k, Geom g);
+__global__ void k_merge_full(VecArg e, int ke, VecArg o, int ko, double2 *__restrict__ full, Geom g);
 
 // dst = src re-stored at another precision (FP16/BF16 quantise per site)
 template <int PIN, int POUT>

@@ -31,6 +31,8 @@ STAG_ERR_STATE = -7
 STAG_FP64, STAG_FP32, STAG_FP16, STAG_BF16 = 0, 1, 2, 3
 STAG_ROUND_OUTPUT = 0x100
 STAG_HALF_VECTORS = 0x200
+STAG_VEC_FP16 = 0x400
+STAG_VEC_BF16 = 0x800
 STAG_ANTIPERIODIC_T = 1
 STAG_RECON12 = 2
 
@@ -77,6 +79,7 @@ def load():
             "stag_dslash_eo": (I, [P, I, P, P]),
             "stag_mdagm": (I, [P, I, D, P, P]),
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
+            "stag_solve_full": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_counters": (I, [P, P, P]),
@@ -84,6 +87,8 @@ def load():
             "stag_solve_stats": (I, [P, I, P, P, P]),
             "stag_mdagm_dot_noalloc": (I, [P, D, P, P, P, P]),
             "stag_force": (I, [P, P, P, P]),
+            "stag_action": (I, [P, D, P, P, P]),
+            "stag_action_backward": (I, [P, P, D, P, P]),
             "stag_cg_solve_ragged": (I, [ctypes.POINTER(SolveDesc), I, D, I, I]),
             "stag_last_error": (ctypes.c_char_p, [P]),
             "stag_status_string": (ctypes.c_char_p, [I]),
@@ -170,6 +175,20 @@ def stag_cg_solve(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, tr
     return st, it, tr
 
 
+def stag_solve_full(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, true_res=None):
+    """Full-lattice M x = b: srcs list of nrhs (V, 3) vectors; xs nrhs*nmass (V, 3) outputs."""
+    lib = load()
+    nrhs, nmass = len(srcs), len(masses)
+    sp = (ctypes.c_void_p * nrhs)(*[_ptr(s) for s in srcs])
+    xp = (ctypes.c_void_p * (nrhs * nmass))(*[_ptr(x) for x in xs])
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    it = np.zeros(nrhs * nmass, np.int32) if iters is None else iters
+    tr = np.zeros(nrhs * nmass, np.float64) if true_res is None else true_res
+    st = lib.stag_solve_full(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
+                             int(precision), xp, it.ctypes.data, tr.ctypes.data)
+    return st, it, tr
+
+
 def stag_time_dslash(ctx, precision, nlaunch):
     ms = ctypes.c_double(0.0)
     by = ctypes.c_double(0.0)
@@ -237,6 +256,19 @@ def stag_cg_solve_ragged(entries, tol, maxiter, precision):
 def stag_force(ctx, x_even, grad_links=None, lie_force=None):
     return load().stag_force(ctx, _ptr(x_even), None if grad_links is None else _ptr(grad_links),
                              None if lie_force is None else _ptr(lie_force))
+
+
+def stag_action(ctx, mass, phi_even, x_even):
+    """(status, S) with S = 2 Re<phi, x> - Re<x, A x> (double-word FP64 sums on the GPU)."""
+    S = ctypes.c_double(0.0)
+    st = load().stag_action(ctx, float(mass), _ptr(phi_even), _ptr(x_even), ctypes.byref(S))
+    return st, S.value
+
+
+def stag_action_backward(ctx, x_even, gS, grad_links=None, grad_phi=None):
+    return load().stag_action_backward(ctx, _ptr(x_even), float(gS),
+                                       None if grad_links is None else _ptr(grad_links),
+                                       None if grad_phi is None else _ptr(grad_phi))
 
 
 def stag_last_error(ctx):
@@ -347,6 +379,27 @@ class Context:
         self._check(st, ok)
         return xs, st, it, tr
 
+    def solve_full(self, srcs, masses, tol=1e-10, maxiter=100000, precision=STAG_FP32, xs=None,
+                   allow_not_converged=False):
+        """Full-lattice M x = b (M = 2m + D); srcs and xs are (V, 3) vectors in
+        lexicographic site order.  Returns (xs, status, iters, true_res)."""
+        if xs is None:
+            xs = []
+            for r in range(len(srcs)):
+                for _ in masses:
+                    try:
+                        import torch
+                        if isinstance(srcs[r], torch.Tensor):
+                            xs.append(torch.empty((self.V, 3), dtype=torch.complex128, device=srcs[r].device))
+                            continue
+                    except ImportError:  # pragma: no cover
+                        pass
+                    xs.append(np.empty((self.V, 3), np.complex128))
+        st, it, tr = stag_solve_full(self.h, srcs, masses, tol, maxiter, precision, xs)
+        ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
+        self._check(st, ok)
+        return xs, st, it, tr
+
     def solve_stats(self, sys=0):
         """(iters, reliable_updates, true_res) of system `sys` of the last solve."""
         st, it, nu, tr = stag_solve_stats(self.h, sys)
@@ -370,6 +423,17 @@ class Context:
             f = np.empty((4, self.V, 8), np.float64) if lie else None
         self._check(stag_force(self.h, x_even, g, f))
         return g, f
+
+    def action(self, phi_even, x_even, mass):
+        """S = phi^dag A^{-1} phi at the solution x_even, stationary form (a float)."""
+        st, S = stag_action(self.h, mass, phi_even, x_even)
+        self._check(st)
+        return S
+
+    def action_backward(self, x_even, gS, grad_links=None, grad_phi=None):
+        """Fill grad_links (4, V, 3, 3) = gS K^dag and grad_phi (V/2, 3) = 2 gS x (either may be None)."""
+        self._check(stag_action_backward(self.h, x_even, gS, grad_links, grad_phi))
+        return grad_links, grad_phi
 
     def time_dslash(self, precision=STAG_FP32, nlaunch=50):
         st, ms, by = stag_time_dslash(self.h, precision, nlaunch)

@@ -87,3 +87,29 @@ def test_config2_twelve_sources_four_masses():
         t = oracle.true_residual(L, U, masses[k], bs[r], xs[j].cpu().numpy())
         assert t <= 1e-10, (j, t)
         assert abs(t - tr[j]) <= 1e-12 + 0.05 * t
+
+
+@pytest.mark.parametrize("vec", ["fp16", "bf16"])
+def test_config2_half_vectors_fp32_links(vec):
+    """The 12-source x 4-mass workload (m = 0.01 ... 0.05) with the Krylov
+    vectors p and D_oe p stored at FP16 / BF16 (per-site scale) and FP32
+    reconstruct-12 links, FP32 arithmetic, FP64 reliable updates: all 48
+    systems reach the 1e-10 true residual (BF16 links do not converge at
+    these masses)."""
+    L = (20, 20, 20, 64)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, synth.seed_for(2, 1))
+    bs = [synth.gaussian_vector(V // 2, synth.seed_for(2, 100 + r)) for r in range(12)]
+    masses = [0.01, 0.02, 0.03, 0.05]
+    P = stag.STAG_FP32 | (stag.STAG_VEC_FP16 if vec == "fp16" else stag.STAG_VEC_BF16)
+    with stag.Context(L, recon12=True) as ctx:
+        ctx.links_upload(torch.from_numpy(U).cuda())
+        xs, st, it, tr = ctx.cg_solve([torch.from_numpy(b).cuda() for b in bs], masses, tol=1e-10,
+                                      maxiter=40000, precision=P)
+        torch.cuda.synchronize()
+    assert st == stag.STAG_OK and np.all(tr <= 1e-10), (stag.status_name(st), tr.max())
+    for j in (0, 13, 26, 47):
+        r, k = divmod(j, len(masses))
+        t = oracle.true_residual(L, U, masses[k], bs[r], xs[j].cpu().numpy())
+        assert t <= 1e-10, (j, t)
+        assert abs(t - tr[j]) <= 1e-12 + 0.05 * t

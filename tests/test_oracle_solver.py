@@ -204,3 +204,18 @@ def test_full_lattice_solve_matches_dense(L, m, c):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10
     r = 2 * m * x + oracle.dslash_full(L, U, x) - b
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-11
+
+
+def test_all_core_build_is_bit_identical():
+    """The -fopenmp timing build of the oracle parallelises only the per-site
+    loop of the operator: its CG returns exactly the serial build's solution."""
+    L = (4, 4, 4, 8)
+    V = oracle.volume(L)
+    U = synth.random_links(L, 0.4, 501)
+    b = synth.gaussian_vector(V // 2, 502)
+    x1, st1, it1, tr1 = oracle.cg(L, U, 0.1, b, tol=1e-10)
+    with oracle.threads(4) as th:
+        assert th.count() >= 1
+        x2, st2, it2, tr2 = oracle.cg(L, U, 0.1, b, tol=1e-10)
+    assert (st1, it1, tr1) == (st2, it2, tr2)
+    assert np.array_equal(x1, x2)
