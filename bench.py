@@ -67,6 +67,8 @@ def parse():
                     help="config number of the input seeds (1000 * config + stream)")
     ap.add_argument("--no-extras", action="store_true",
                     help="profiling runs: skip the comparison solves, the e2e leg and the CPU baseline")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched / 48^3x96 extras (config 2, ragged, config 4, HBM-bound kernels)")
     return ap.parse_args()
 
 
@@ -228,20 +230,136 @@ def sum_over_ranks(dist, value, device):
     return float(t.item())
 
 
-def cpu_oracle_sample(L, U, b, mass, budget_s):
-    """The FP64 oracle's CG for a bounded number of iterations on this workload."""
+def cpu_oracle_sample(L, U, b, mass, budget_s, threads=1):
+    """The FP64 oracle's CG for a bounded number of iterations on this workload,
+    single-threaded or (threads = 0: every host core) with the all-core build
+    (only the operator's per-site loop parallel; results bit-identical).
+    Returns (GFLOP/s, iterations, seconds, threads used)."""
     import oracle
-    t = time.perf_counter()
-    oracle.mdagm(L, U, mass, b)
-    t1 = time.perf_counter() - t
-    n = max(2, int(budget_s / max(t1, 1e-3)))
-    t = time.perf_counter()
-    _, st, it, _ = oracle.cg(L, U, mass, b, tol=1e-300, maxiter=n)
-    dt = time.perf_counter() - t
+
+    def run():
+        t = time.perf_counter()
+        oracle.mdagm(L, U, mass, b)
+        t1 = time.perf_counter() - t
+        n = max(2, int(budget_s / max(t1, 1e-3)))
+        t = time.perf_counter()
+        _, st, it, _ = oracle.cg(L, U, mass, b, tol=1e-300, maxiter=n)
+        return it, time.perf_counter() - t
+
+    if threads == 1:
+        used = 1
+        it, dt = run()
+    else:
+        with oracle.threads(threads) as th:
+            used = th.count()
+            it, dt = run()
     Ve = (L[0] * L[1] * L[2] * L[3]) // 2
     # the oracle also recomputes the true residual once (one more operator application)
     gflops = FLOP_PER_SITE_ITER * Ve * it / dt / 1e9
-    return gflops, it, dt
+    return gflops, it, dt, used
+
+
+def timed_solve(ctx, srcs, masses, prec, tol, maxiter, stream):
+    """One solve timed with CUDA events on the solver's stream, after an
+    untimed 16-iteration call that tunes the launch form and builds the graph.
+    Returns a dict of time, iterations and worst true residual."""
+    import torch
+
+    from paper_1511_00088_gb300 import stag
+    ctx.cg_solve(srcs, masses, tol=tol, maxiter=16, precision=prec, allow_not_converged=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xs, st, it, tr = ctx.cg_solve(srcs, masses, tol=tol, maxiter=maxiter, precision=prec,
+                                  allow_not_converged=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    Ve = ctx.Ve
+    return {"ms": ms, "systems": len(it), "iters_max": int(max(it)), "iters_sum": int(sum(it)),
+            "true_res_max": float(max(tr)), "status": stag.status_name(st),
+            "TFLOP/s": FLOP_PER_SITE_ITER * Ve * float(sum(it)) / (ms * 1e-3) / 1e12,
+            "launch_form": ctx.solve_form()}
+
+
+def batched_extras(stream, hbm):
+    """Driver-visible numbers of the batched workloads and the HBM-bound
+    lattice: 12 sources x 4 masses on 20^3x64 (FP32 and FP16/BF16 Krylov
+    vectors, FP32 reconstruct-12 links), the ragged batch of four lattices in
+    one graph, and on 48^3x96 the two CG kernels at one source (links far
+    larger than L2: algorithmic bytes / time is DRAM-honest there) and the
+    16-source m = 0.005 solve against one FP64 single-source solve."""
+    import torch
+
+    from paper_1511_00088_gb300 import stag, synth
+    out = {}
+    tol = 1e-10
+    V32 = stag.STAG_FP32
+    # configuration 2: 12 sources x 4 masses on 20^3 x 64
+    L = (20, 20, 20, 64)
+    V = synth.volume(L)
+    U = torch.from_numpy(synth.random_links(L, 0.4, synth.seed_for(2, 1))).cuda()
+    bs = [torch.from_numpy(synth.gaussian_vector(V // 2, synth.seed_for(2, 100 + r))).cuda() for r in range(12)]
+    masses = [0.01, 0.02, 0.03, 0.05]
+    c2 = {}
+    with stag.Context(L, recon12=True, stream=stream.cuda_stream) as ctx:
+        ctx.links_upload(U)
+        for name, p in (("fp32", V32), ("fp32_links_fp16_vectors", V32 | stag.STAG_VEC_FP16),
+                        ("fp32_links_bf16_vectors", V32 | stag.STAG_VEC_BF16)):
+            c2[name] = timed_solve(ctx, bs, masses, p, tol, 40000, stream)
+        c2["fp64_one_system_m0.01"] = timed_solve(ctx, bs[:1], masses[:1], stag.STAG_FP64, tol, 40000, stream)
+    out["config2_12src_x_4mass_20x64"] = c2
+    del U, bs
+    # the ragged batch: one source x the 4 masses on each of four lattices, one graph
+    ctxs, batch = [], []
+    try:
+        for n, Lr in enumerate([(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), (20, 20, 20, 64)]):
+            Vr = synth.volume(Lr)
+            c = stag.Context(Lr, recon12=True, stream=stream.cuda_stream)
+            c.links_upload(torch.from_numpy(synth.random_links(Lr, 0.4, synth.seed_for(2, 10 * n + 1))).cuda())
+            ctxs.append(c)
+            batch.append((c, [torch.from_numpy(synth.gaussian_vector(Vr // 2, synth.seed_for(2, 10 * n + 2)))
+                              .cuda()], masses))
+        stag.cg_solve_ragged(batch, tol=tol, maxiter=16, precision=V32, allow_not_converged=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st, its, trs = stag.cg_solve_ragged(batch, tol=tol, maxiter=40000, precision=V32,
+                                               allow_not_converged=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        flop = sum(FLOP_PER_SITE_ITER * c.Ve * float(sum(it)) for c, it in zip(ctxs, its))
+        out["ragged_4_lattices_4_masses"] = {
+            "lattices": [list(c.dims) for c in ctxs], "sites": sum(c.V for c in ctxs), "ms": ms,
+            "iters_max": int(max(max(it) for it in its)), "true_res_max": float(max(max(t) for t in trs)),
+            "status": stag.status_name(st), "TFLOP/s": flop / (ms * 1e-3) / 1e12}
+    finally:
+        for c in ctxs:
+            c.close()
+    # 48^3 x 96: HBM-bound kernels and configuration 4
+    L = (48, 48, 48, 96)
+    V = synth.volume(L)
+    U = synth.random_links_device(L, 0.4, synth.seed_for(4, 1), device="cuda")
+    with stag.Context(L, recon12=True, stream=stream.cuda_stream) as ctx:
+        ctx.links_upload(U)
+        del U
+        kern = {}
+        for name, p in (("fp32", V32), ("fp32_links_bf16_vectors", V32 | stag.STAG_VEC_BF16)):
+            for kk in (0, 1):
+                ms_k, by_k = ctx.time_cg_kernel(kk, p, nlaunch=50)
+                gbs = by_k / (ms_k * 1e-3) / 1e9
+                kern[f"{name}_k{kk + 1}"] = {"ms_per_launch": ms_k, "algorithmic_bytes_per_launch": by_k,
+                                            "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm}
+        out["hbm_bound_48x96_one_source"] = kern
+        bs = [torch.from_numpy(synth.gaussian_vector(V // 2, synth.seed_for(4, 2 + r))).cuda() for r in range(16)]
+        c4 = {"mixed_fp32_r12_16src": timed_solve(ctx, bs, [0.005], V32, tol, 40000, stream),
+              "fp64_one_source": timed_solve(ctx, bs[:1], [0.005], stag.STAG_FP64, tol, 40000, stream)}
+        c4["speedup_per_source_vs_fp64"] = c4["fp64_one_source"]["ms"] / (c4["mixed_fp32_r12_16src"]["ms"] / 16)
+        out["config4_48x96_16src_m0.005"] = c4
+    return out
 
 
 def run_reference(args):
@@ -256,20 +374,21 @@ def run_reference(args):
     b = synth.gaussian_vector(V // 2, synth.seed_for(1, 2))
     vals, times = [], []
     for i in range(args.warmup + args.steps):
-        g, it, dt = cpu_oracle_sample(L, U, b, args.mass, 6.0)
+        g, it, dt, used = cpu_oracle_sample(L, U, b, args.mass, 6.0, threads=0)
         if i >= args.warmup:
             vals.append(g)
             times.append(dt)
     value = statistics.mean(vals)
-    sample = f"{it} FP64 CG iterations of the CPU oracle per step on the {L} field, single thread"
+    sample = (f"{it} FP64 CG iterations of the CPU oracle per step on the {L} field, {used} threads "
+              f"(all host cores; the operator's per-site loop in parallel)")
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": workload_config(L, args.mass, args.tol, "fp64"),
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": used, "kind": "oracle",
+                         "sample": sample, "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -436,15 +555,20 @@ def run_ours(args):
                                         "GFLOP/s": DSLASH_FLOP_PER_SITE * Ve / (m * 1e-3) / 1e9}
         # FP64 single-source time over the timed solve's time per source
         extras["mixed_vs_fp64_speedup"] = extras["cg_fp64"]["ms"] / (total_ms / args.steps / nsys)
+        if not args.no_batched and nsys == 1 and L == (20, 20, 20, 64):
+            extras["batched"] = batched_extras(stream, hbm)
 
     cpu = None
     if ws == 1 and rank == 0 and not args.no_extras:
         if U is None:
             U = Ud.cpu().numpy()
-        g, it, dt = cpu_oracle_sample(L, U, b, masses[0], 12.0)
-        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+        g1, it1, dt1, _ = cpu_oracle_sample(L, U, b, masses[0], 10.0, threads=1)
+        g, it, dt, used = cpu_oracle_sample(L, U, b, masses[0], 10.0, threads=0)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": used, "kind": "oracle", "nproc": os.cpu_count(),
                "sample": f"{it} FP64 CG iterations of the CPU oracle on the same {L} field "
-                         f"({dt:.1f} s, single thread)"}
+                         f"({dt:.1f} s, {used} threads: the operator's per-site loop in parallel)",
+               "single_thread": {"value": g1, "unit": "GFLOP/s", "cores": 1,
+                                 "sample": f"{it1} FP64 CG iterations ({dt1:.1f} s, one thread)"}}
 
     if rank == 0:
         line = {

@@ -236,8 +236,10 @@ def test_benchmarked_form_full_size_against_oracle():
     x = xs[0].cpu().numpy()
     tr_o = check_solution(L, U, m, b, x, tr[0])
     with oracle.threads():
-        xo, st_o, it_o, tro = oracle.cg(L, U, m, b, tol=1e-11, maxiter=20000)
-    assert st_o == 0 and tro <= 1e-11
+        # plain FP64 CG: its iterated residual stops at 5e-11, the recomputed one
+        # (a few 1e-12 above it at this conditioning) stays below 1e-10
+        xo, st_o, it_o, tro = oracle.cg(L, U, m, b, tol=5e-11, maxiter=20000)
+    assert tro <= 1e-10, (st_o, it_o, tro)
     # |x - x*| <= |b - A x| / lambda_min, lambda_min >= 4 m^2
     err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
     bound = (tr_o + tro) * np.linalg.norm(b) / (4 * m * m) / np.linalg.norm(xo)
