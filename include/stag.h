@@ -158,6 +158,28 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
                   int iters[], double true_res[]);
 
 /*
+ * stag_cg_solve for several masses by a multi-shift CG (Sec. 3's inverter
+ * with its multi-mass workloads): the systems of one source differ only by the
+ * shift 4 m^2, so the masses share one Krylov space -- one operator
+ * application per iteration serves them all:
+ *   phase 1  the smallest mass runs the mixed-precision CG of stag_cg_solve
+ *            (FP64 reliable updates) and the other masses follow its
+ *            residuals as shifted systems (r_s = zeta_s r; FP32 directions and
+ *            solutions), each until its estimated residual is below 1e-5;
+ *   phase 2  each shifted system continues from that solution as an initial
+ *            guess with the mixed-precision CG (its first step recomputes
+ *            b - A x0 in FP64) to the tolerance.
+ * Phase 2 is needed: FP32 shifted recurrences stall near eps_32 kappa_s of
+ * their systems, and reliable updates cannot act on them (they would break
+ * r_s = zeta_s r).  Arguments, layouts and statuses as stag_cg_solve;
+ * iters[] counts both phases; precision must be a reduced one (not
+ * STAG_FP64).  stag_solve_stats/counters/form then describe phase 2.
+ */
+int stag_cg_solve_multishift(stag_ctx *ctx, const double *const src[], int nrhs, const double masses[],
+                             int nmass, double tol, int maxiter, int precision, double *const x[], int iters[],
+                             double true_res[]);
+
+/*
  * Solve the full-lattice staggered equation M x = b, M = 2m + D (the operator
  * at the top of this header with its mass term; Sec. 3 of the paper: the
  * equation the CG inverter serves, its even-site Schur complement being what

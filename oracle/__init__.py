@@ -66,6 +66,7 @@ def _bind(path):
         "orc_true_residual": (D, [P, I, P, D, P, P]),
         "orc_cg": (I, [P, I, P, D, P, P, D, I, P, P]),
         "orc_solve_full": (I, [P, I, P, D, P, P, D, I, P, P]),
+        "orc_cg_masses": (I, [P, I, P, I, P, P, P, D, I, P, P]),
         "orc_round_format": (D, [D, I, I]),
         "orc_quantize_vectors": (None, [I, L, P, P]),
         "orc_round_links": (None, [I, L, P, P]),
@@ -229,6 +230,20 @@ def cg(L, links, mass, b, tol=1e-10, maxiter=100000, antiperiodic=True):
     st = lib.orc_cg(_p(d), int(antiperiodic), _p(U), float(mass), _p(bb), _p(x), float(tol),
                     int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     return x, int(st), int(it.value), float(tr.value)
+
+
+def cg_masses(L, links, masses, b, tol=1e-10, maxiter=100000, antiperiodic=True):
+    """Plain FP64 CG for every mass (the shifted systems of one source), each
+    independently.  Returns (xs (nmass, V/2, 3), worst status, iters, true_res)."""
+    lib = _load()
+    d, U, bb = _dims(L), _c128(links), _c128(b)
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    x = np.empty((len(m),) + bb.shape, np.complex128)
+    it = np.zeros(len(m), np.int32)
+    tr = np.zeros(len(m), np.float64)
+    st = lib.orc_cg_masses(_p(d), int(antiperiodic), _p(U), len(m), _p(m), _p(bb), _p(x), float(tol),
+                           int(maxiter), _p(it), _p(tr))
+    return x, int(st), it, tr
 
 
 def solve_full(L, links, mass, b_full, tol=1e-12, maxiter=100000, antiperiodic=True):

@@ -311,6 +311,27 @@ int orc_cg(const int L[4], int antiperiodic, const double *U, double mass, const
 }
 
 /*
+ * Several masses, one source (the multi-mass solves of the Sec. 3 workloads:
+ * the shifted systems (4 m_k^2 - D_eo D_oe) x_k = b, shift 4 m_k^2): the
+ * solutions are unique, so the oracle of a multi-shift solver is the plain
+ * CG above run for each mass independently.  x holds nmass vectors of 6 Ve
+ * doubles, one after the other; iters/true_res one entry per mass.  Returns
+ * the worst orc_cg status (0 when every mass converged).
+ */
+int orc_cg_masses(const int L[4], int antiperiodic, const double *U, int nmass, const double *masses,
+                  const double *b, double *x, double tol, int maxiter, int *iters_out, double *true_res_out)
+{
+    long n = 6 * (volume(L) / 2);
+    int worst = 0;
+    for (int k = 0; k < nmass; ++k) {
+        int st = orc_cg(L, antiperiodic, U, masses[k], b, x + k * n, tol, maxiter,
+                        iters_out ? iters_out + k : NULL, true_res_out ? true_res_out + k : NULL);
+        if (st != 0 && (worst == 0 || st < worst)) worst = st;
+    }
+    return worst;
+}
+
+/*
  * The full-lattice staggered equation M x = b with M = 2m + D (the equation
  * the inverter of Sec. 3 solves; the even-site CG above is its Schur
  * complement).  With M = [[2m, D_eo], [D_oe, 2m]] on (even, odd):

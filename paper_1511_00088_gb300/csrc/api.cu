@@ -128,6 +128,7 @@ struct Work {
   int tma = 0;                     // link path of the CG kernels (DsArgs::tma)
   int l2p = 0;                     // their links persist in L2 during a solve
   int mrhs = 0;                    // > 0: the CG kernels are k_dslash_mrhs with mrhs systems per block
+  int ms = 0;                      // > 0: multi-shift CG, ms shifted systems ride on each system
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
@@ -198,6 +199,9 @@ struct stag_ctx {
   VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
   VecBuf full_e, full_o, full_x;  // full-lattice solve: halves of the sources, odd half of a solution
   DevBuf red;                     // block sums of the action's reduction
+  VecBuf ms_p, ms_x;              // multi-shift CG: shifted directions and solutions (FP32)
+  DevBuf ms_sh;                   // their ShiftState
+  PinnedBuf ms_h;
   DevBuf defect;
   Work w;
   int last_nsys = 0;  // systems of the most recent solve (stats in w.h_st)
@@ -677,11 +681,15 @@ int tune_lanes(stag_ctx *c, int LP, int recon, int VP, int NS, int G, int nsys, 
 Ctl work_ctl(stag_ctx *c, bool graph);
 DsArgs ds_base(stag_ctx *c);
 
-int work_prepare(stag_ctx *c, int nsys, int precision) {
+int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
   Work &w = c->w;
   int prec, VP, RP;
   if (!solver_precs(precision, &prec, &VP, &RP)) return arg_err(c, "bad solver precision");
   const int recon = link_recon(c, prec);
+  if (w.ms != ms) {  // the shift kernel enters or leaves the graph's loop body
+    w.drop_graph();
+    w.ms = ms;
+  }
   if (w.nsys == nsys && w.prec == prec && w.VP == VP && w.recon == recon) return STAG_OK;
   w.drop_graph();
   c->last_nsys = 0;
@@ -882,6 +890,33 @@ cudaError_t launch_cg(stag_ctx *c, int kernel, int epi, cudaStream_t s, const Ds
   return launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi, kernel == 0 ? w.lanes_k1 : w.lanes_k2, nb, s, a);
 }
 
+// The shifted-system update of a multi-shift solve (w.ms > 0), launched
+// between the two CG kernels; `fold` as the second kernel's (the first
+// kernel's sums in fold_partials over states ctl.st), or FIN_NONE with the
+// states already finalized.
+constexpr double MS_SHIFT_TOL = 1e-5;  // shifts stop below this estimated residual (under their FP32 floor)
+
+int launch_ms(stag_ctx *c, cudaStream_t s, const DsArgs &k2) {
+  Work &w = c->w;
+  MsArgs m;
+  memset(&m, 0, sizeof m);
+  m.d = k2;
+  m.nsh = w.ms;
+  m.r = w.r.arg();
+  m.ps = c->ms_p.arg();
+  m.xs = c->ms_x.arg();
+  m.sh = (ShiftState *)c->ms_sh.p;
+  m.tol2 = MS_SHIFT_TOL * MS_SHIFT_TOL;
+  // blocks per base system: enough to cover the SMs with the systems together
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  const int full = (c->Ve + 127) / 128;
+  int nbx = (8 * nsm + w.nsys - 1) / w.nsys;
+  m.nbx = nbx < full ? (nbx < 1 ? 1 : nbx) : full;
+  CK(launch_shift_update(m, s));
+  return STAG_OK;
+}
+
 // One CG iteration with a finalize kernel after each CG kernel (the form
 // without folded reductions, STAG_FOLD=0): K1, its finalize, K2, its finalize.
 int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
@@ -919,6 +954,11 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
     a.fin = FIN_ALPHA;
     CK(launch_cg(c, 0, EPI_CG_K1, s, a));
     CK(launch_finalize(ctl, FIN_ALPHA, nbx, 2, w.nsys, s, c->pdl));
+  }
+  if (w.ms > 0) {
+    DsArgs m = a;
+    m.fold = FIN_NONE;
+    CKS(launch_ms(c, s, m));
   }
   // K2: p = r + beta p_old; Ap = 4 m^2 p - D_eo t; r -= alpha Ap; x += alpha p; |r|^2
   a.par_out = 0;
@@ -993,6 +1033,7 @@ int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
     a.fold_nbx = w.nbx_k1;
     a.fold_nv = rec ? 1 : 2;
     a.st_out = S[1 - cur];
+    if (w.ms > 0) CKS(launch_ms(c, s, a));
     CK(launch_cg(c, 1, EPI_CG_K2, s, a));
     cur = 1 - cur;
   }
@@ -1465,6 +1506,92 @@ int op_impl(stag_ctx *c, int which, int precision, double mass, const double *in
   return STAG_OK;
 }
 
+// Multi-shift CG (several masses of each source on one Krylov space), then a
+// per-mass mixed-precision refinement:
+//  phase 1: the base systems (the smallest mass) run the CG of stag_cg_solve
+//    with its reliable updates; the other masses ride on it as shifts (the
+//    shift kernel between the two CG kernels) until their estimated residual
+//    zeta |r| falls below MS_SHIFT_TOL |b| -- the FP32 recurrences leave them
+//    at about eps_32 kappa_s of their own systems, whatever the base does;
+//  phase 2: every shifted system is solved from its phase-1 solution as the
+//    initial guess (one batched solve; its first step recomputes r = b - A x0
+//    in FP64) to the tolerance.
+int ms_impl(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass, double tol,
+            int maxiter, int prec, double *const x[], int iters[], double true_res[]) {
+  int k0 = 0;
+  for (int k = 1; k < nmass; ++k)
+    if (masses[k] * masses[k] < masses[k0] * masses[k0]) k0 = k;
+  std::vector<int> sk;  // user index of each shift
+  std::vector<double> sm;
+  for (int k = 0; k < nmass; ++k)
+    if (k != k0) {
+      sk.push_back(k);
+      sm.push_back(masses[k]);
+    }
+  const int nsh = nmass - 1, nsys2 = nrhs * nsh, Ve = c->Ve;
+  // phase 1
+  CKS(work_prepare(c, nrhs, prec, nsh));
+  Work &w = c->w;
+  const void *lo = nullptr;
+  CKS(links_for(c, w.prec, &lo));
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 *d = nullptr;
+    CKS(vec_in(c, src[r], c->stage_in, 0, &d));
+    CK(launch_pack_vec(P64, d, w.b64.arg(), r, Ve, c->stream));
+  }
+  CK(c->ms_p.ensure(P32, nsys2, Ve));
+  CK(c->ms_x.ensure(P32, nsys2, Ve));
+  CK(c->ms_sh.ensure(sizeof(ShiftState) * nsys2));
+  CK(c->ms_h.ensure(sizeof(ShiftState) * nsys2));
+  CK(cudaMemsetAsync(c->ms_p.data.p, 0, cplx_bytes(P32) * 3ull * nsys2 * Ve, c->stream));
+  CK(cudaMemsetAsync(c->ms_x.data.p, 0, cplx_bytes(P32) * 3ull * nsys2 * Ve, c->stream));
+  ShiftState *hs = (ShiftState *)c->ms_h.p;
+  CK(cudaStreamSynchronize(c->stream));  // the pinned staging buffer is free
+  for (int r = 0; r < nrhs; ++r)
+    for (int q = 0; q < nsh; ++q) {
+      ShiftState &h = hs[r * nsh + q];
+      memset(&h, 0, sizeof h);
+      h.dm4 = 4.0 * sm[q] * sm[q] - 4.0 * masses[k0] * masses[k0];
+      h.zeta = h.zeta_prev = h.alpha_prev = 1.0;
+      h.active = 1;
+    }
+  CK(cudaMemcpyAsync(c->ms_sh.p, hs, sizeof(ShiftState) * nsys2, cudaMemcpyHostToDevice, c->stream));
+  const double m0[1] = {masses[k0]};
+  CKS(solve_start(c, m0, 1, tol, maxiter, nullptr));
+  CKS(solve_run(c, maxiter));
+  CK(cudaMemcpyAsync(w.h_st.p, w.st.p, sizeof(SysState) * nrhs, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hs, c->ms_sh.p, sizeof(ShiftState) * nsys2, cudaMemcpyDeviceToHost, c->stream));
+  for (int r = 0; r < nrhs; ++r) CKS(vec_out(c, w.x64, r, x[r * nmass + k0]));
+  std::vector<int> it1(nrhs), it2(nsys2);
+  std::vector<double> tr1(nrhs), tr2(nsys2);
+  const int st1 = solve_status(c, it1.data(), tr1.data());
+  if (st1 < 0) return st1;
+  std::vector<int> ms_it(nsys2);
+  for (int j = 0; j < nsys2; ++j) ms_it[j] = hs[j].iter;
+  // phase 2: the shifted systems from their phase-1 solutions
+  CKS(solve_stage(c, src, nrhs, sm.data(), nsh, tol, maxiter, prec));
+  CK(launch_convert_vec(P32, P64, c->ms_x.arg(), w.x64.arg(), nsys2, Ve, c->stream));
+  CK(launch_mark_update(w.st.p ? (SysState *)w.st.p : nullptr, nsys2, c->stream));
+  CKS(enqueue_update(c, c->stream, work_ctl(c, false)));
+  CKS(solve_run(c, maxiter));
+  CK(cudaMemcpyAsync(w.h_st.p, w.st.p, sizeof(SysState) * nsys2, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, c->stream));
+  for (int r = 0; r < nrhs; ++r)
+    for (int q = 0; q < nsh; ++q) CKS(vec_out(c, w.x64, r * nsh + q, x[r * nmass + sk[q]]));
+  const int st2 = solve_status(c, it2.data(), tr2.data());
+  for (int r = 0; r < nrhs; ++r) {
+    if (iters) iters[r * nmass + k0] = it1[r];
+    if (true_res) true_res[r * nmass + k0] = tr1[r];
+    for (int q = 0; q < nsh; ++q) {
+      if (iters) iters[r * nmass + sk[q]] = ms_it[r * nsh + q] + it2[r * nsh + q];
+      if (true_res) true_res[r * nmass + sk[q]] = tr2[r * nsh + q];
+    }
+  }
+  if (st2 < 0) return st2;
+  return (st1 == STAG_OK && st2 == STAG_OK) ? STAG_OK : STAG_NOT_CONVERGED;
+}
+
 // out = D in (FP64) on the sites of parity par_out, one system
 int apply_m64_plain(stag_ctx *c, int par_out, VecArg in, VecArg out) {
   int lanes = 1;
@@ -1852,6 +1979,35 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_cg_solve_multishift(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,
+                             double tol, int maxiter, int precision, double *const x[], int iters[],
+                             double true_res[]) {
+  if (!c) return STAG_ERR_ARG;
+  if (!src || !masses || !x) return arg_err(c, "NULL argument");
+  if (nrhs < 1 || nmass < 1) return arg_err(c, "nrhs and nmass must be >= 1");
+  if ((long long)nrhs * nmass > 4096) return arg_err(c, "at most 4096 systems per solve");
+  if (!(tol > 0.0) || !(tol < 1.0)) return arg_err(c, "tol must be in (0, 1)");
+  if (maxiter < 1) return arg_err(c, "maxiter must be >= 1");
+  {
+    int lp, vp, rp;
+    if (!solver_precs(precision, &lp, &vp, &rp)) return arg_err(c, "bad solver precision");
+    if (rp != P32) return arg_err(c, "multi-shift CG needs a reduced-precision inner iteration (not STAG_FP64)");
+  }
+  for (int r = 0; r < nrhs; ++r)
+    if (!src[r]) return arg_err(c, "NULL source");
+  for (int j = 0; j < nrhs * nmass; ++j)
+    if (!x[j]) return arg_err(c, "NULL solution buffer");
+  for (int k = 0; k < nmass; ++k)
+    if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
+  CK(cudaSetDevice(c->device));
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  if (nmass == 1) return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+  return ms_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
 }
 
 int stag_solve_full(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,

@@ -217,7 +217,7 @@ cudaError_t launch_convert_vec(int PIN, int POUT, VecArg src, VecArg dst, int ns
     return cudaGetLastError();                                                 \
   }
   STAG_CV(P16, P32) STAG_CV(PBF, P32) STAG_CV(P32, P16) STAG_CV(P32, PBF)
-  STAG_CV(P64, P16) STAG_CV(P64, PBF) STAG_CV(P64, P32)
+  STAG_CV(P64, P16) STAG_CV(P64, PBF) STAG_CV(P64, P32) STAG_CV(P32, P64)
 #undef STAG_CV
   return cudaErrorNotSupported;
 }

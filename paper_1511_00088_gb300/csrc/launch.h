@@ -90,6 +90,11 @@ cudaError_t launch_dslash_mrhs(int LP, int recon, int nsw, int EPI, int nblocks,
                                const void **kptr = nullptr);
 
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
+// multi-shift CG (multishift.cu): the shifted-system update between the two CG
+// kernels (a.nbx blocks per base system), and the pending-update mark of a
+// solve from an initial guess
+cudaError_t launch_shift_update(const MsArgs &a, cudaStream_t st);
+cudaError_t launch_mark_update(SysState *st, int nsys, cudaStream_t s);
 // k_finalize over the partials of the kernel just launched: nbx blocks per
 // system group, nv values per system (pdl: launched as a programmatic
 // dependent of that kernel)

@@ -161,6 +161,31 @@ struct DsArgs {
   float l2_hit;
 };
 
+// Multi-shift CG: the shifted systems (A_0 + dm4) x_s = b of one source ride
+// on the Krylov space of the base system A_0 (the smallest mass).  Shift
+// recurrence (exact for r_s = zeta_s r), per base iteration k with the base's
+// alpha_k, beta_{k-1}:
+//   zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+//                (alpha_k beta_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} alpha_{k-1} (1 + dm4 alpha_k))
+//   p_s = zeta_k r_k + beta_{k-1} (zeta_k / zeta_{k-1})^2 p_s;  x_s += alpha_k (zeta_{k+1} / zeta_k) p_s
+// with zeta_0 = zeta_{-1} = 1, alpha_{-1} = 1, beta_{-1} = 0, p_s = 0.
+struct ShiftState {
+  double dm4;         // 4 m_s^2 - 4 m_0^2 (>= 0)
+  double zeta, zeta_prev, alpha_prev;
+  int active;         // 1 while the shift's recurrence runs
+  int iter;           // base iterations it took part in
+};
+
+struct MsArgs {
+  DsArgs d;           // nsys base systems; ctl.st = their states; the fold of the first CG kernel's sums
+  int nsh;            // shifts per base system
+  VecArg r;           // base residuals r_k (FP32, [nsys])
+  VecArg ps, xs;      // shifted directions and solutions (FP32, [nsys * nsh], slot j * nsh + q)
+  ShiftState *sh;     // [nsys * nsh]
+  double tol2;        // a shift stops when zeta_{k+1}^2 |r_k|^2 <= tol2 |b|^2
+  int nbx;            // blocks per base system
+};
+
 struct BlasArgs {
   int Ve;
   VecArg p, r, x, b, x64, t;   // meanings per kernel

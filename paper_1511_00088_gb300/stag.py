@@ -80,6 +80,7 @@ def load():
             "stag_mdagm": (I, [P, I, D, P, P]),
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_solve_full": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
+            "stag_cg_solve_multishift": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_counters": (I, [P, P, P]),
@@ -172,6 +173,20 @@ def stag_cg_solve(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, tr
     tr = np.zeros(nrhs * nmass, np.float64) if true_res is None else true_res
     st = lib.stag_cg_solve(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
                            int(precision), xp, it.ctypes.data, tr.ctypes.data)
+    return st, it, tr
+
+
+def stag_cg_solve_multishift(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, true_res=None):
+    """As stag_cg_solve, by a multi-shift CG plus per-mass refinement."""
+    lib = load()
+    nrhs, nmass = len(srcs), len(masses)
+    sp = (ctypes.c_void_p * nrhs)(*[_ptr(s) for s in srcs])
+    xp = (ctypes.c_void_p * (nrhs * nmass))(*[_ptr(x) for x in xs])
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    it = np.zeros(nrhs * nmass, np.int32) if iters is None else iters
+    tr = np.zeros(nrhs * nmass, np.float64) if true_res is None else true_res
+    st = lib.stag_cg_solve_multishift(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
+                                      int(precision), xp, it.ctypes.data, tr.ctypes.data)
     return st, it, tr
 
 
@@ -375,6 +390,16 @@ class Context:
         if xs is None:
             xs = [self._like(srcs[r]) for r in range(len(srcs)) for _ in masses]
         st, it, tr = stag_cg_solve(self.h, srcs, masses, tol, maxiter, precision, xs)
+        ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
+        self._check(st, ok)
+        return xs, st, it, tr
+
+    def cg_solve_multishift(self, srcs, masses, tol=1e-10, maxiter=100000, precision=STAG_FP32, xs=None,
+                            allow_not_converged=False):
+        """Multi-shift CG; returns (xs, status, iters, true_res) like cg_solve."""
+        if xs is None:
+            xs = [self._like(srcs[r]) for r in range(len(srcs)) for _ in masses]
+        st, it, tr = stag_cg_solve_multishift(self.h, srcs, masses, tol, maxiter, precision, xs)
         ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
         self._check(st, ok)
         return xs, st, it, tr

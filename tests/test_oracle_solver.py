@@ -219,3 +219,23 @@ def test_all_core_build_is_bit_identical():
         x2, st2, it2, tr2 = oracle.cg(L, U, 0.1, b, tol=1e-10)
     assert (st1, it1, tr1) == (st2, it2, tr2)
     assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("L,c", [((2, 2, 2, 2), 0.7), ((4, 2, 2, 4), 0.5)])
+def test_cg_masses_matches_dense_solves(L, c):
+    """The multi-mass oracle (one source, several shifts 4 m^2) against a dense
+    LU solve of each assembled A_m, and each mass's own CG."""
+    U = synth.random_links(L, c, 121)
+    b = synth.gaussian_vector(synth.volume(L) // 2, 122)
+    masses = [0.03, 0.07, 0.2, 0.5]
+    xs, st, it, tr = oracle.cg_masses(L, U, masses, b, tol=1e-12)
+    assert st == 0 and np.all(tr <= 1e-12)
+    for k, m in enumerate(masses):
+        A = dense_A(L, U, m)
+        xd = np.linalg.solve(A, b.reshape(-1)).reshape(-1, 3)
+        kappa = np.linalg.cond(A)
+        assert np.linalg.norm(xs[k] - xd) / np.linalg.norm(xd) <= 10 * kappa * 1e-12
+        x1, _, it1, _ = oracle.cg(L, U, m, b, tol=1e-12)
+        assert np.array_equal(xs[k], x1) and it[k] == it1
+    # heavier masses need fewer iterations
+    assert list(it) == sorted(it, reverse=True)
