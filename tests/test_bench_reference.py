@@ -21,7 +21,9 @@ def test_reference_arm_json_line():
     assert d["dtype"] == "f64" and d["data"] == "synthetic" and d["vs_baseline"] is None
     assert d["ms_per_step"] > 0 and "workload" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["sample"]
+    # all host cores (the oracle's all-core build), the count recorded
+    assert cb["nproc"] == os.cpu_count() and 1 <= cb["cores"] <= cb["nproc"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
