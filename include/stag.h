@@ -277,9 +277,11 @@ int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps
  * registers), out[5] 1 when the links persist in L2 during the solve, out[6]
  * CG iterations per pass of the solve loop, out[7] 1 when the CG kernels
  * share each chunk's links in shared memory among the out[0] systems of a
- * block (one warp per system).  Implementation detail of this library (the
- * paper has no counterpart), for reports.  STAG_ERR_ARG before the first
- * solve.
+ * block (one warp per system), 2 when every block runs every system on
+ * links staged once per tile in shared memory (out[0] = the systems,
+ * out[2] = out[3] = threads per site).  Implementation detail of this
+ * library (the paper has no counterpart), for reports.  STAG_ERR_ARG before
+ * the first solve.
  */
 int stag_solve_form(const stag_ctx *ctx, int out[8]);
 

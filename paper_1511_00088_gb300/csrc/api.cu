@@ -129,6 +129,8 @@ struct Work {
   int l2p = 0;                     // their links persist in L2 during a solve
   int mrhs = 0;                    // > 0: the CG kernels are k_dslash_mrhs with mrhs systems per block
   int ms = 0;                      // > 0: multi-shift CG, ms shifted systems ride on each system
+  int nrhs_sl = 0;                 // > 0: the CG kernels are k_cg_nrhs (every system in every block,
+                                   // the links staged once per tile), nrhs_sl threads per site
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
@@ -498,6 +500,52 @@ int time_mrhs_pair(stag_ctx *c, int recon, int nsw, DsArgs a1, DsArgs a2, float 
   return STAG_OK;
 }
 
+// Blocks of k_cg_nrhs with sl threads per site: one wave of resident
+// blocks, at most one per tile of LT sites.
+int nrhs_blocks(stag_ctx *c, int recon, int sl, int EPI, int *nb) {
+  const int full = (c->Ve + LT - 1) / LT;
+  DsArgs none;
+  memset(&none, 0, sizeof none);
+  const void *k = nullptr;
+  CK(launch_cg_nrhs(recon, sl, EPI, 0, c->stream, none, &k));
+  int per_sm = 0, nsm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * sl, cg_nrhs_smem(recon)));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  int n = per_sm * nsm;
+  if (n < 1) n = 1;
+  *nb = n < full ? n : full;
+  return STAG_OK;
+}
+
+// total time of 2 sweeps of tune_pairs() alternating launch pairs of the two
+// k_cg_nrhs kernels (the measure tune_cg_pair reports; no finalize between)
+int time_nrhs_pair(stag_ctx *c, int recon, int sl, DsArgs a1, DsArgs a2, float *ms_out) {
+  int n1 = 0, n2 = 0;
+  CKS(nrhs_blocks(c, recon, sl, EPI_CG_K1R, &n1));
+  CKS(nrhs_blocks(c, recon, sl, EPI_CG_K2, &n2));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float tot = 0.f;
+  const int np = tune_pairs(c);
+  for (int o = 0; o < 2; ++o) {
+    for (int i = 0; i < np + 2; ++i) {
+      if (i == 2) CK(cudaEventRecord(e0, c->stream));
+      CK(launch_cg_nrhs(recon, sl, EPI_CG_K1R, n1, c->stream, a1));
+      CK(launch_cg_nrhs(recon, sl, EPI_CG_K2, n2, c->stream, a2));
+    }
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    tot += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = tot;
+  return STAG_OK;
+}
+
 struct CgForm {
   int tma = 0, l1 = 1, l2 = 1, l2p = 0;  // link path, lanes of the two kernels, L2-persisting links
 };
@@ -780,6 +828,28 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
     const char *fmr = getenv("STAG_MRHS");
     if (fmr && (fmr[0] == '4' || fmr[0] == '8') && fmr[1] == 0 && prec == P32 && VP == P32 && nsys >= 2)
       cands.assign(1, 100 + (fmr[0] - '0'));
+    // k_cg_nrhs (every system in every block, the links staged once per tile in
+    // shared memory): FP32 links and vectors, 2..64 systems; encoded 200 + sl
+    const bool nrhs_ok = prec == P32 && VP == P32 && nsys >= 2 && nsys <= CG_NRHS_MAX;
+    if (nrhs_ok && !(fns && fns[0] != 0) && !(fmr && fmr[0] != 0)) {
+      cands.push_back(202);
+      cands.push_back(204);
+    }
+    const char *fnr = getenv("STAG_NRHS");  // 2 or 4: this form with that many threads per site; 0: never
+    if (fnr && (fnr[0] == '2' || fnr[0] == '4') && fnr[1] == 0 && nrhs_ok) cands.assign(1, 200 + (fnr[0] - '0'));
+    if (fnr && fnr[0] == '0' && fnr[1] == 0) {
+      std::vector<int> keep;
+      for (int v : cands)
+        if (v < 200) keep.push_back(v);
+      cands = keep;
+    }
+    const void *tiled = nullptr;
+    for (int v : cands)
+      if (v > 200) {
+        CKS(links_tile_for(c, prec, &tiled));
+        a.links_tile = a2.links_tile = tiled;
+        break;
+      }
     int best_ns = cands[0];
     if (cands.size() > 1) {
       const TuneKey nkey(prec, recon, VP, 2000 + nsys, tma_ok ? 1 : 0, c->dims[0], c->dims[1], c->dims[2],
@@ -798,7 +868,9 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
         float best_ms = 1e30f;
         for (int ns : cands) {
           float ms = -1.f;
-          if (ns > 100) {
+          if (ns > 200) {
+            CKS(time_nrhs_pair(c, recon, ns - 200, a, a2, &ms));
+          } else if (ns > 100) {
             CKS(time_mrhs_pair(c, recon, ns - 100, a, a2, &ms));
           } else {
             a.ngroups = a2.ngroups = (nsys + ns - 1) / ns;
@@ -815,11 +887,21 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
         tune_cache_store(nkey, best_ns);
       }
     }
-    w.mrhs = best_ns > 100 ? best_ns - 100 : 0;
-    w.NS = w.mrhs ? w.mrhs : best_ns;
+    w.nrhs_sl = best_ns > 200 ? best_ns - 200 : 0;
+    w.mrhs = (best_ns > 100 && best_ns < 200) ? best_ns - 100 : 0;
+    w.NS = w.mrhs ? w.mrhs : (w.nrhs_sl ? 1 : best_ns);
     w.G = (nsys + w.NS - 1) / w.NS;
     a.ngroups = a2.ngroups = w.G;
-    if (w.mrhs) {
+    if (w.nrhs_sl) {
+      // the BLAS and update kernels keep one system per group; the CG kernels
+      // are one grid of nbx_k1 / nbx_k2 blocks, each a partial per system
+      CKS(links_tile_for(c, prec, &w.links_tile));
+      w.tma = 1;
+      w.lanes_k1 = w.lanes_k2 = w.nrhs_sl;
+      w.l2p = 0;
+      CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K1R, &w.nbx_k1));
+      CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K2, &w.nbx_k2));
+    } else if (w.mrhs) {
       w.tma = 0;
       w.lanes_k1 = w.lanes_k2 = 1;
       w.l2p = 0;
@@ -885,6 +967,8 @@ BlasArgs blas_base(stag_ctx *c, const Ctl &ctl) {
 // kernel 1: EPI_CG_K2) in the workspace's tuned launch form.
 cudaError_t launch_cg(stag_ctx *c, int kernel, int epi, cudaStream_t s, const DsArgs &a) {
   Work &w = c->w;
+  if (w.nrhs_sl)
+    return launch_cg_nrhs(w.recon, w.nrhs_sl, epi, kernel == 0 ? w.nbx_k1 : w.nbx_k2, s, a);
   const int nb = (kernel == 0 ? w.nbx_k1 : w.nbx_k2) * w.G;
   if (w.mrhs) return launch_dslash_mrhs(w.prec, w.recon, w.mrhs, epi, nb, s, a);
   return launch_dslash(w.prec, w.recon, w.VP, w.VP, w.NS, epi, kernel == 0 ? w.lanes_k1 : w.lanes_k2, nb, s, a);
@@ -980,7 +1064,9 @@ int enqueue_main(stag_ctx *c, cudaStream_t s, const Ctl &ctl) {
 // the states in w.st.
 int enqueue_pass(stag_ctx *c, cudaStream_t s, const Ctl &ctl, int unroll) {
   Work &w = c->w;
-  if (!c->fold) {
+  // k_cg_nrhs does not fold its predecessor's sums (each block holds every
+  // system): a finalize kernel follows each CG kernel
+  if (!c->fold || w.nrhs_sl) {
     for (int u = 0; u < unroll; ++u) CKS(enqueue_main(c, s, ctl));
     return STAG_OK;
   }
@@ -2133,7 +2219,11 @@ int stag_solve_form(const stag_ctx *c, int out[8]) {
   out[4] = w.tma;
   out[5] = w.l2p;
   out[6] = solve_unroll();
-  out[7] = w.mrhs ? 1 : 0;
+  out[7] = w.mrhs ? 1 : (w.nrhs_sl ? 2 : 0);
+  if (w.nrhs_sl) {
+    out[0] = w.nsys;  // every system in every block
+    out[1] = 1;
+  }
   return STAG_OK;
 }
 

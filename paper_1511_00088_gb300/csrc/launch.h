@@ -89,6 +89,14 @@ cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int la
 cudaError_t launch_dslash_mrhs(int LP, int recon, int nsw, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                                const void **kptr = nullptr);
 
+// k_cg_nrhs<recon, EPI, sl> (nrhs.cu): the two CG kernels for nsys <= 64
+// systems, FP32 links (tiled copy, a.links_tile) and vectors, sl = 2 or 4
+// threads per site; nblocks blocks stride over tiles of LT sites; kptr as above
+cudaError_t launch_cg_nrhs(int recon, int sl, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
+                           const void **kptr = nullptr);
+unsigned cg_nrhs_smem(int recon);
+constexpr int CG_NRHS_MAX = 64;
+
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);
 // multi-shift CG (multishift.cu): the shifted-system update between the two CG
 // kernels (a.nbx blocks per base system), and the pending-update mark of a
