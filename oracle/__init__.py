@@ -73,6 +73,8 @@ def _bind(path):
         "orc_force_K": (None, [P, I, P, P, P]),
         "orc_force_lie": (None, [L, P, P, P]),
         "orc_set_threads": (None, [I]),
+        "orc_su3_project": (None, [P, P]),
+        "orc_hyp": (None, [P, P, P, P]),
         "orc_threads": (I, []),
     }
     for name, (res, args) in sig.items():
@@ -257,6 +259,35 @@ def solve_full(L, links, mass, b_full, tol=1e-12, maxiter=100000, antiperiodic=T
     st = lib.orc_solve_full(_p(d), int(antiperiodic), _p(U), float(mass), _p(bb), _p(x), float(tol),
                             int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     return x, int(st), int(it.value), float(tr.value)
+
+
+HYP_ALPHA = (0.75, 0.6, 0.3)
+
+
+def su3_project(X):
+    """P(X): unitary polar factor (Newton's iteration) with the determinant's
+    phase removed by the principal cube root; X (..., 3, 3)."""
+    lib = _load()
+    X = _c128(X)
+    out = np.empty_like(X)
+    flat_in = X.reshape(-1, 3, 3)
+    flat_out = out.reshape(-1, 3, 3)
+    for k in range(flat_in.shape[0]):
+        a = np.ascontiguousarray(flat_in[k])
+        b = np.empty_like(a)
+        lib.orc_su3_project(_p(a), _p(b))
+        flat_out[k] = b
+    return out
+
+
+def hyp(L, links, alpha=HYP_ALPHA):
+    """HYP-smeared links (4, V, 3, 3) of `links` (Hasenfratz-Knechtli levels)."""
+    lib = _load()
+    d, U = _dims(L), _c128(links)
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+    out = np.empty_like(U)
+    lib.orc_hyp(_p(d), _p(U), _p(a), _p(out))
+    return out
 
 
 def round_format(v, mant_bits, emin):

@@ -17,6 +17,7 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_oracle_hyp as hy
 from tests import test_oracle_operator as op
 from tests import test_oracle_solver as sv
 
@@ -62,6 +63,23 @@ MUTANTS = {
         "bt[k] = 2.0 * mass * be[k] - t[k];", "bt[k] = be[k] - t[k];"),
     "full solve: odd sites without 1/(2m)": (
         "xo[k] = (bo[k] - t[k]) / (2.0 * mass);", "xo[k] = (bo[k] - t[k]) / mass;"),
+    "HYP level 3 staple weight a1/4": (
+        "c_scale(a1 / 6.0, acc[k])", "c_scale(a1 / 4.0, acc[k])"),
+    "HYP level 2 thin weight": (
+        "c_scale(1.0 - a2, u[k])", "c_scale(1.0 - a3, u[k])"),
+    "HYP staple's last link not daggered": (
+        "m_dag(fc(cc, d, xmu), cd);", "for (int k = 0; k < 9; ++k) cd[k] = fc(cc, d, xmu)[k];"),
+    "HYP negative staple starts at x+d": (
+        "shifted(L, x, d, -1, xmd);", "shifted(L, x, d, 1, xmd);"),
+    "HYP level 2 decorated by nu": (
+        "int sdir = 6 - mu - nu - rho; /* 0+1+2+3 = 6 */", "int sdir = nu;"),
+    "HYP level 3 side links decorated by nu": (
+        "fctx side = {Vt, V, L, mu}, mid = {Vt, V, L, nu};", "fctx side = {Vt, V, L, nu}, mid = {Vt, V, L, nu};"),
+    "projection keeps the determinant phase": (
+        "for (int k = 0; k < 9; ++k) W[k] = c_mul(Y[k], rot);", "for (int k = 0; k < 9; ++k) W[k] = Y[k];"),
+    "multi-mass oracle reuses the first mass": (
+        "int st = orc_cg(L, antiperiodic, U, masses[k], b, x + k * n, tol, maxiter,",
+        "int st = orc_cg(L, antiperiodic, U, masses[0], b, x + k * n, tol, maxiter,"),
 }
 
 
@@ -76,6 +94,13 @@ def _pins():
     yield lambda: sv.test_cg_degenerate_cases()
     yield lambda: sv.test_force_central_differences((2, 2, 2, 4))
     yield lambda: sv.test_full_lattice_solve_matches_dense((2, 2, 2, 2), 0.05, 0.7)
+    yield lambda: sv.test_cg_masses_matches_dense_solves((2, 2, 2, 2), 0.7)
+    yield hy.test_projection_against_svd_polar_factor
+    yield hy.test_output_is_su3_and_smooths
+    yield hy.test_gauge_covariance
+    for d in range(4):
+        yield lambda d=d: hy.test_translation_invariance(d)
+    yield hy.test_first_order_response_by_path_counting
 
 
 @pytest.fixture(scope="module")
