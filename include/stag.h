@@ -158,6 +158,27 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
                   int iters[], double true_res[]);
 
 /*
+ * HYP smearing of a gauge field (Sec. 3: the quarks are "HYP-smeared"
+ * staggered quarks; the paper gives no parameters): links_out = the
+ * hypercubic-blocked field of links_in by Hasenfratz and Knechtli's three
+ * levels of decorated staples,
+ *   Vb(x,mu;e)  = P[(1-a3) U_mu(x) + a3/2 sum_{+-e} U_e U_mu U_e^dag],  e != mu,
+ *   Vt(x,mu;nu) = P[(1-a2) U_mu(x) + a2/4 sum_{+-r != mu,nu} Vb(r;s) Vb(mu;s) Vb(r;s)^dag],
+ *                 s = the direction outside {mu, nu, r},
+ *   V(x,mu)     = P[(1-a1) U_mu(x) + a1/6 sum_{+-nu != mu} Vt(nu;mu) Vt(mu;nu) Vt(nu;mu)^dag],
+ * with P(X) the unitary polar factor of X with its determinant's phase removed
+ * (principal cube root), so every output link is SU(3).
+ *   alpha      (a1, a2, a3); NULL = (0.75, 0.6, 0.3);
+ *   links_in, links_out  [4][V][3][3][2] FP64 as stag_links_upload, host or
+ *              device; they may be the same buffer.
+ * FP64 throughout on the GPU; the context provides the lattice and the
+ * stream (its gauge field is not touched: upload the result to use it).
+ * Scratch: 2 x 12 V links of the context's device memory.
+ * Errors: STAG_ERR_ARG, STAG_ERR_CUDA, STAG_ERR_OOM.
+ */
+int stag_hyp_smear(stag_ctx *ctx, const double alpha[3], const double *links_in, double *links_out);
+
+/*
  * stag_cg_solve for several masses by a multi-shift CG (Sec. 3's inverter
  * with its multi-mass workloads): the systems of one source differ only by the
  * shift 4 m^2, so the masses share one Krylov space -- one operator

@@ -201,6 +201,7 @@ struct stag_ctx {
   VecBuf api_a, api_b, api_c;  // internal vectors of the operator calls
   VecBuf full_e, full_o, full_x;  // full-lattice solve: halves of the sources, odd half of a solution
   DevBuf red;                     // block sums of the action's reduction
+  DevBuf hyp_b, hyp_t, hyp_io;    // HYP smearing: the two decorated levels, host staging
   VecBuf ms_p, ms_x;              // multi-shift CG: shifted directions and solutions (FP32)
   DevBuf ms_sh;                   // their ShiftState
   PinnedBuf ms_h;
@@ -2065,6 +2066,34 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_hyp_smear(stag_ctx *c, const double alpha[3], const double *links_in, double *links_out) {
+  if (!c) return STAG_ERR_ARG;
+  if (!links_in || !links_out) return arg_err(c, "NULL links");
+  double a[3] = {0.75, 0.6, 0.3};
+  if (alpha) {
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(alpha[k])) return arg_err(c, "non-finite smearing parameter");
+      a[k] = alpha[k];
+    }
+  }
+  CK(cudaSetDevice(c->device));
+  const size_t bytes = sizeof(double) * 18ull * 4ull * c->V;
+  const bool in_dev = is_device_ptr(links_in), out_dev = is_device_ptr(links_out);
+  CK(c->hyp_b.ensure(sizeof(double) * 18ull * 12ull * c->V));
+  CK(c->hyp_t.ensure(sizeof(double) * 18ull * 12ull * c->V));
+  if (!in_dev || !out_dev) CK(c->hyp_io.ensure(bytes));
+  const double2 *U = reinterpret_cast<const double2 *>(links_in);
+  if (!in_dev) {
+    CK(cudaMemcpyAsync(c->hyp_io.p, links_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    U = reinterpret_cast<const double2 *>(c->hyp_io.p);
+  }
+  double2 *out = out_dev ? reinterpret_cast<double2 *>(links_out) : reinterpret_cast<double2 *>(c->hyp_io.p);
+  CK(launch_hyp(c->dims, U, a, (double2 *)c->hyp_b.p, (double2 *)c->hyp_t.p, out, c->stream));
+  if (!out_dev) CK(cudaMemcpyAsync(links_out, c->hyp_io.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
 }
 
 int stag_cg_solve_multishift(stag_ctx *c, const double *const src[], int nrhs, const double masses[], int nmass,

@@ -1,0 +1,277 @@
+// hyp.cu -- HYP smearing of the gauge field on the GPU (FP64): the one-link
+// field of the "HYP-smeared staggered quarks" whose CG Sec. 3 benchmarks.
+//
+// Three levels of decorated links, each a projection to SU(3) of the thin link
+// plus a weighted staple sum over the level below, staples kept inside the
+// hypercubes of the link (parameters (a1, a2, a3), Hasenfratz-Knechtli's
+// (0.75, 0.6, 0.3) by default):
+//   Vb(x,mu;e)  = P[(1-a3) U_mu(x) + a3/2 sum_{+-e} U_e U_mu U_e^dag]              (e != mu)
+//   Vt(x,mu;nu) = P[(1-a2) U_mu(x) + a2/4 sum_{+-r, r != mu,nu} Vb(r;s) Vb(mu;s) Vb(r;s)^dag]
+//                 (s = the direction outside {mu, nu, r})
+//   V(x,mu)     = P[(1-a1) U_mu(x) + a1/6 sum_{+-nu != mu} Vt(nu;mu) Vt(mu;nu) Vt(nu;mu)^dag]
+// A positive staple in direction d at x is W_d(x) W_mu(x+d) W_d(x+mu)^dag,
+// a negative one W_d(x-d)^dag W_mu(x-d) W_d(x-d+mu).
+// P(X) = the unitary polar factor of X with the phase of its determinant
+// removed by the principal cube root.  Here the polar factor comes from
+// Newton's iteration with determinant scaling (Y <- (g Y + (g Y)^-dag) / 2,
+// g = |det Y|^(-1/3); Higham, "Computing the polar decomposition", 1986),
+// which reaches the same unique factor in fewer steps than the plain one.
+// One thread per (decorated link, site); links in the ABI layout
+// [direction][site][3][3] complex (decorated: [12 (mu, decoration) slots][site][3][3]).
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace stag {
+
+namespace {
+
+struct M3 {
+  double2 a[9];
+};
+
+__device__ __forceinline__ double2 cm(double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); }
+__device__ __forceinline__ double2 cadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
+__device__ __forceinline__ double2 csub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
+__device__ __forceinline__ double2 ccj(double2 x) { return make_double2(x.x, -x.y); }
+
+__device__ __forceinline__ M3 ld(const double2 *p) {
+  M3 m;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m.a[k] = p[k];
+  return m;
+}
+
+// c = a b, with either factor optionally daggered
+template <bool DA, bool DB>
+__device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
+  M3 c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double2 x = DA ? ccj(a.a[k * 3 + i]) : a.a[i * 3 + k];
+        const double2 y = DB ? ccj(b.a[j * 3 + k]) : b.a[k * 3 + j];
+        s = cadd(s, cm(x, y));
+      }
+      c.a[i * 3 + j] = s;
+    }
+  return c;
+}
+
+__device__ __forceinline__ double2 det3(const M3 &m) {
+  const double2 *a = m.a;
+  const double2 t0 = csub(cm(a[4], a[8]), cm(a[5], a[7]));
+  const double2 t1 = csub(cm(a[5], a[6]), cm(a[3], a[8]));
+  const double2 t2 = csub(cm(a[3], a[7]), cm(a[4], a[6]));
+  return cadd(cadd(cm(a[0], t0), cm(a[1], t1)), cm(a[2], t2));
+}
+
+// P(X): scaled Newton polar iteration, then the determinant's phase removed
+__device__ M3 project_su3(const M3 &X) {
+  M3 Y = X;
+  for (int it = 0; it < 60; ++it) {
+    const double2 d = det3(Y);
+    const double ad = sqrt(d.x * d.x + d.y * d.y);
+    const double g = (it < 6) ? cbrt(1.0 / ad) : 1.0;  // scaling only while far from unitary
+    // (g Y)^-dag = (1/g) adj(Y)^dag / conj(det Y): entry (i, j) = conj(cof_ij(Y)) / (g conj(det))
+    const double inv = 1.0 / (g * (d.x * d.x + d.y * d.y));
+    M3 N;
+    double diff = 0.0, nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+        const double2 cof = csub(cm(Y.a[r0 * 3 + c0], Y.a[r1 * 3 + c1]), cm(Y.a[r0 * 3 + c1], Y.a[r1 * 3 + c0]));
+        // conj(cof) / conj(d) = conj(cof / d) = conj(cof conj(d)) / |d|^2
+        const double2 q = ccj(cm(cof, ccj(d)));
+        const double2 yid = make_double2(q.x * inv, q.y * inv);
+        const double2 n = make_double2(0.5 * (g * Y.a[i * 3 + j].x + yid.x), 0.5 * (g * Y.a[i * 3 + j].y + yid.y));
+        const double2 e = csub(n, Y.a[i * 3 + j]);
+        diff += e.x * e.x + e.y * e.y;
+        nrm += n.x * n.x + n.y * n.y;
+        N.a[i * 3 + j] = n;
+      }
+    Y = N;
+    if (it >= 6 && diff <= 1e-32 * nrm) break;
+  }
+  const double2 d = det3(Y);
+  const double ph = atan2(d.y, d.x) / 3.0;
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  const double2 rot = make_double2(cs, -sn);
+  M3 W;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) W.a[k] = cm(Y.a[k], rot);
+  return W;
+}
+
+struct Lat {
+  int L[4];
+  long long V;
+};
+
+__device__ __forceinline__ void coords(const Lat &g, long long i, int (&x)[4]) {
+  x[0] = (int)(i % g.L[0]);
+  i /= g.L[0];
+  x[1] = (int)(i % g.L[1]);
+  i /= g.L[1];
+  x[2] = (int)(i % g.L[2]);
+  x[3] = (int)(i / g.L[2]);
+}
+
+__device__ __forceinline__ long long lexs(const Lat &g, const int (&x)[4], int d, int s, int d2 = -1, int s2 = 0) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  y[d] = (y[d] + s + g.L[d]) % g.L[d];
+  if (d2 >= 0) y[d2] = (y[d2] + s2 + g.L[d2]) % g.L[d2];
+  return y[0] + (long long)g.L[0] * (y[1] + (long long)g.L[1] * (y[2] + (long long)g.L[2] * y[3]));
+}
+
+// slot of the decorated link (dir, deco != dir) among the 12 stored: [dir][3]
+__device__ __forceinline__ int dslot(int dir, int deco) { return dir * 3 + (deco < dir ? deco : deco - 1); }
+
+// a field of links: thin (deco < 0: [dir][V]) or decorated ([12][V], slot dslot(dir, deco))
+struct Fld {
+  const double2 *p;
+  long long V;
+  __device__ __forceinline__ const double2 *at(int dir, int deco, long long site) const {
+    return deco < 0 ? p + ((long long)dir * V + site) * 9 : p + ((long long)dslot(dir, deco) * V + site) * 9;
+  }
+};
+
+// acc += the two staples in direction d of the link (x, mu): side links of
+// field A with decoration da, middle link of field B with decoration db
+__device__ __forceinline__ void staples(const Lat &g, const int (&x)[4], long long i, int mu, int d, const Fld &A,
+                                        int da, const Fld &B, int db, M3 &acc) {
+  // + d: A_d(x) B_mu(x+d) A_d(x+mu)^dag
+  {
+    const M3 a = ld(A.at(d, da, i));
+    const M3 b = ld(B.at(mu, db, lexs(g, x, d, 1)));
+    const M3 c = ld(A.at(d, da, lexs(g, x, mu, 1)));
+    const M3 t = mul<false, false>(a, b);
+    const M3 s = mul<false, true>(t, c);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+  }
+  // - d: A_d(x-d)^dag B_mu(x-d) A_d(x-d+mu)
+  {
+    const long long xm = lexs(g, x, d, -1);
+    const M3 a = ld(A.at(d, da, xm));
+    const M3 b = ld(B.at(mu, db, xm));
+    const M3 c = ld(A.at(d, da, lexs(g, x, d, -1, mu, 1)));
+    const M3 t = mul<true, false>(a, b);
+    const M3 s = mul<false, false>(t, c);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+  }
+}
+
+__device__ __forceinline__ void smear_store(const double2 *u, double a, double w, const M3 &acc, double2 *out) {
+  M3 X;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X.a[k] = make_double2((1.0 - a) * u[k].x + w * acc.a[k].x, (1.0 - a) * u[k].y + w * acc.a[k].y);
+  const M3 W = project_su3(X);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[k] = W.a[k];
+}
+
+// level 1: thread over (mu, e != mu, site); Vb stored [dslot(mu, e)][V]
+__global__ void k_hyp1(Lat g, const double2 *U, double a3, double2 *Vb) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 12 * g.V) return;
+  const long long i = t % g.V;
+  const int pr = (int)(t / g.V), mu = pr / 3, e = (pr % 3 >= mu) ? pr % 3 + 1 : pr % 3;
+  int x[4];
+  coords(g, i, x);
+  const Fld thin{U, g.V};
+  M3 acc;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.a[k] = make_double2(0.0, 0.0);
+  staples(g, x, i, mu, e, thin, -1, thin, -1, acc);
+  smear_store(thin.at(mu, -1, i), a3, a3 / 2.0, acc, Vb + ((long long)dslot(mu, e) * g.V + i) * 9);
+}
+
+// level 2: thread over (mu, nu != mu, site); Vt stored [dslot(mu, nu)][V]
+__global__ void k_hyp2(Lat g, const double2 *U, const double2 *Vb, double a2, double2 *Vt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 12 * g.V) return;
+  const long long i = t % g.V;
+  const int pr = (int)(t / g.V), mu = pr / 3, nu = (pr % 3 >= mu) ? pr % 3 + 1 : pr % 3;
+  int x[4];
+  coords(g, i, x);
+  const Fld vb{Vb, g.V};
+  M3 acc;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.a[k] = make_double2(0.0, 0.0);
+  for (int r = 0; r < 4; ++r) {
+    if (r == mu || r == nu) continue;
+    const int s = 6 - mu - nu - r;  // the direction outside {mu, nu, r}
+    staples(g, x, i, mu, r, vb, s, vb, s, acc);
+  }
+  smear_store(U + ((long long)mu * g.V + i) * 9, a2, a2 / 4.0, acc, Vt + ((long long)dslot(mu, nu) * g.V + i) * 9);
+}
+
+// level 3: thread over (mu, site); out may alias U (each thread reads only its own thin link)
+__global__ void k_hyp3(Lat g, const double2 *U, const double2 *Vt, double a1, double2 *out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * g.V) return;
+  const long long i = t % g.V;
+  const int mu = (int)(t / g.V);
+  int x[4];
+  coords(g, i, x);
+  const Fld vt{Vt, g.V};
+  M3 acc;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.a[k] = make_double2(0.0, 0.0);
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    // sides Vt(., nu; mu), middle Vt(., mu; nu)
+    // + nu
+    {
+      const M3 a = ld(vt.at(nu, mu, i));
+      const M3 b = ld(vt.at(mu, nu, lexs(g, x, nu, 1)));
+      const M3 c = ld(vt.at(nu, mu, lexs(g, x, mu, 1)));
+      const M3 s = mul<false, true>(mul<false, false>(a, b), c);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+    }
+    // - nu
+    {
+      const long long xm = lexs(g, x, nu, -1);
+      const M3 a = ld(vt.at(nu, mu, xm));
+      const M3 b = ld(vt.at(mu, nu, xm));
+      const M3 c = ld(vt.at(nu, mu, lexs(g, x, nu, -1, mu, 1)));
+      const M3 s = mul<false, false>(mul<true, false>(a, b), c);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+    }
+  }
+  double2 u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[((long long)mu * g.V + i) * 9 + k];
+  smear_store(u, a1, a1 / 6.0, acc, out + ((long long)mu * g.V + i) * 9);
+}
+
+}  // namespace
+
+cudaError_t launch_hyp(const int dims[4], const double2 *U, const double alpha[3], double2 *Vb, double2 *Vt,
+                       double2 *out, cudaStream_t st) {
+  Lat g;
+  for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
+  g.V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  const int bt = 128;
+  k_hyp1<<<(unsigned)((12 * g.V + bt - 1) / bt), bt, 0, st>>>(g, U, alpha[2], Vb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_hyp2<<<(unsigned)((12 * g.V + bt - 1) / bt), bt, 0, st>>>(g, U, Vb, alpha[1], Vt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_hyp3<<<(unsigned)((4 * g.V + bt - 1) / bt), bt, 0, st>>>(g, U, Vt, alpha[0], out);
+  return cudaGetLastError();
+}
+
+}  // namespace stag

@@ -125,6 +125,11 @@ cudaError_t launch_pack_links_tiled(int LP, int recon, const double2 *src, void 
 cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
                               cudaStream_t st);
 
+// HYP smearing (hyp.cu): out [4][V][3][3] = the smeared links of U (same
+// layout; out may alias U); Vb, Vt scratch of 12 V links each; alpha = (a1, a2, a3)
+cudaError_t launch_hyp(const int dims[4], const double2 *U, const double alpha[3], double2 *Vb, double2 *Vt,
+                       double2 *out, cudaStream_t st);
+
 // k_force over all 4 V links (force.cu): X even, Y = D_oe X odd (device SoA,
 // FP64); grad [4][V][3][3] complex and/or lie [4][V][8] (either may be null)
 cudaError_t launch_force(Geom g, const double2 *X, const double2 *Y, const void *links64, double2 *grad,

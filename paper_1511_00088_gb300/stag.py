@@ -81,6 +81,7 @@ def load():
             "stag_cg_solve": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_solve_full": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_cg_solve_multishift": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
+            "stag_hyp_smear": (I, [P, P, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_counters": (I, [P, P, P]),
@@ -174,6 +175,12 @@ def stag_cg_solve(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, tr
     st = lib.stag_cg_solve(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
                            int(precision), xp, it.ctypes.data, tr.ctypes.data)
     return st, it, tr
+
+
+def stag_hyp_smear(ctx, alpha, links_in, links_out):
+    """HYP smearing; alpha None = (0.75, 0.6, 0.3)."""
+    a = None if alpha is None else np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+    return load().stag_hyp_smear(ctx, None if a is None else a.ctypes.data, _ptr(links_in), _ptr(links_out))
 
 
 def stag_cg_solve_multishift(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, true_res=None):
@@ -393,6 +400,17 @@ class Context:
         ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
         self._check(st, ok)
         return xs, st, it, tr
+
+    def hyp_smear(self, links, alpha=None, out=None):
+        """HYP-smeared copy of links (4, V, 3, 3) complex128 (out may be links)."""
+        if out is None:
+            try:
+                import torch
+                out = torch.empty_like(links) if isinstance(links, torch.Tensor) else np.empty_like(links)
+            except ImportError:  # pragma: no cover
+                out = np.empty_like(links)
+        self._check(stag_hyp_smear(self.h, alpha, links, out))
+        return out
 
     def cg_solve_multishift(self, srcs, masses, tol=1e-10, maxiter=100000, precision=STAG_FP32, xs=None,
                             allow_not_converged=False):
