@@ -309,6 +309,39 @@ def batched_extras(stream, hbm):
                         ("fp32_links_bf16_vectors", V32 | stag.STAG_VEC_BF16)):
             c2[name] = timed_solve(ctx, bs, masses, p, tol, 40000, stream)
         c2["fp64_one_system_m0.01"] = timed_solve(ctx, bs[:1], masses[:1], stag.STAG_FP64, tol, 40000, stream)
+        # the same 48 systems by the multi-shift CG (the 4 masses of a source on
+        # one Krylov space, then each refined from that solution)
+        ctx.cg_solve_multishift(bs, masses, tol=tol, maxiter=16, precision=V32, allow_not_converged=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st, it, tr = ctx.cg_solve_multishift(bs, masses, tol=tol, maxiter=40000, precision=V32,
+                                                allow_not_converged=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        c2["fp32_multishift"] = {"ms": ms, "systems": len(it), "iters_max": int(max(it)),
+                                 "iters_sum": int(sum(it)), "true_res_max": float(max(tr)),
+                                 "status": stag.status_name(st)}
+        # the full-lattice equation M x = b (one source, m = 0.01) and HYP smearing of the field
+        bfull = torch.from_numpy(synth.gaussian_vector(V, synth.seed_for(2, 300))).cuda()
+        ctx.solve_full([bfull], [0.01], tol=tol, maxiter=16, precision=V32, allow_not_converged=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, st, it, tr = ctx.solve_full([bfull], [0.01], tol=tol, maxiter=40000, precision=V32)
+        e1.record(stream)
+        e1.synchronize()
+        out["full_lattice_solve_20x64_m0.01"] = {"ms": e0.elapsed_time(e1), "iters": int(it[0]),
+                                                 "true_res": float(tr[0]), "status": stag.status_name(st)}
+        H = ctx.hyp_smear(U)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.hyp_smear(U, out=H)
+        e1.record(stream)
+        e1.synchronize()
+        out["hyp_smear_20x64_fp64"] = {"ms": e0.elapsed_time(e1), "links": 4 * V}
+        del H
     out["config2_12src_x_4mass_20x64"] = c2
     del U, bs
     # the ragged batch: one source x the 4 masses on each of four lattices, one graph

@@ -130,7 +130,8 @@ struct Work {
   int mrhs = 0;                    // > 0: the CG kernels are k_dslash_mrhs with mrhs systems per block
   int ms = 0;                      // > 0: multi-shift CG, ms shifted systems ride on each system
   int nrhs_sl = 0;                 // > 0: the CG kernels are k_cg_nrhs (every system in every block,
-                                   // the links staged once per tile), nrhs_sl threads per site
+                                   // the links staged once per tile): threads per site, + 10 with
+                                   // one link stage
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
@@ -510,7 +511,7 @@ int nrhs_blocks(stag_ctx *c, int recon, int sl, int EPI, int *nb) {
   const void *k = nullptr;
   CK(launch_cg_nrhs(recon, sl, EPI, 0, c->stream, none, &k));
   int per_sm = 0, nsm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * sl, cg_nrhs_smem(recon)));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * (sl % 10), cg_nrhs_smem(recon, sl)));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   int n = per_sm * nsm;
   if (n < 1) n = 1;
@@ -835,9 +836,15 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
     if (nrhs_ok && !(fns && fns[0] != 0) && !(fmr && fmr[0] != 0)) {
       cands.push_back(202);
       cands.push_back(204);
+      cands.push_back(214);
     }
-    const char *fnr = getenv("STAG_NRHS");  // 2 or 4: this form with that many threads per site; 0: never
-    if (fnr && (fnr[0] == '2' || fnr[0] == '4') && fnr[1] == 0 && nrhs_ok) cands.assign(1, 200 + (fnr[0] - '0'));
+    // STAG_NRHS = 2 or 4: this form with that many threads per site (two link
+    // stages), 14: 4 threads per site with one stage; 0: never this form
+    const char *fnr = getenv("STAG_NRHS");
+    if (fnr && nrhs_ok) {
+      const int f = atoi(fnr);
+      if (f == 2 || f == 4 || f == 14) cands.assign(1, 200 + f);
+    }
     if (fnr && fnr[0] == '0' && fnr[1] == 0) {
       std::vector<int> keep;
       for (int v : cands)
@@ -898,7 +905,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
       // are one grid of nbx_k1 / nbx_k2 blocks, each a partial per system
       CKS(links_tile_for(c, prec, &w.links_tile));
       w.tma = 1;
-      w.lanes_k1 = w.lanes_k2 = w.nrhs_sl;
+      w.lanes_k1 = w.lanes_k2 = w.nrhs_sl % 10;
       w.l2p = 0;
       CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K1R, &w.nbx_k1));
       CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K2, &w.nbx_k2));

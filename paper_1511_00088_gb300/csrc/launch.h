@@ -89,12 +89,13 @@ cudaError_t launch_dslash_pbf(int recon, int VP, int OP, int NS, int EPI, int la
 cudaError_t launch_dslash_mrhs(int LP, int recon, int nsw, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                                const void **kptr = nullptr);
 
-// k_cg_nrhs<recon, EPI, sl> (nrhs.cu): the two CG kernels for nsys <= 64
-// systems, FP32 links (tiled copy, a.links_tile) and vectors, sl = 2 or 4
-// threads per site; nblocks blocks stride over tiles of LT sites; kptr as above
-cudaError_t launch_cg_nrhs(int recon, int sl, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
+// k_cg_nrhs (nrhs.cu): the two CG kernels for nsys <= 64 systems, FP32
+// links (tiled copy, a.links_tile) and vectors; form = sl (2 or 4 threads per
+// site, two link stages) or 10 + sl (one stage, 3 blocks per SM; sl = 4);
+// nblocks blocks stride over tiles of LT sites; kptr as above
+cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr = nullptr);
-unsigned cg_nrhs_smem(int recon);
+unsigned cg_nrhs_smem(int recon, int form);
 constexpr int CG_NRHS_MAX = 64;
 
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);

@@ -26,26 +26,99 @@ namespace stag {
 
 constexpr int NRHS_MAX = 64;  // systems per launch
 
-// dynamic shared memory: two stages of one tile's stored links, plus (reconstruct-12) the full copy
-inline unsigned nrhs_smem_bytes(int recon) {
-  const unsigned tile = 8u * (recon ? 6u : 9u) * (unsigned)LT * 8u;
-  return 2u * tile + (recon ? 8u * 9u * (unsigned)LT * 8u : 0u);
+// The SU(3) x colour-vector products on Blackwell's packed FP32x2 FMA: with
+// v_b = (re, im) and w_b = (-im, re), a complex multiply-accumulate is
+//   h += Re(U_ab) v_b + Im(U_ab) w_b                      (U v)
+//   h += Re(U_ba) v_b - Im(U_ba) w_b                      (U^dag v)
+// two packed FMAs instead of four scalar ones (the links come from shared
+// memory as (re, im) pairs, the vectors are held as pairs).
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+// acc += sgn U v
+__device__ __forceinline__ void mv_x2(const float2 *u, int ls, const float2 (&v)[3], float sgn, float2 (&acc)[3]) {
+  float2 w[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) w[b] = make_float2(-v[b].y, v[b].x);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2 e = u[(3 * a + b) * ls];
+      h = __ffma2_rn(bc2(e.x), v[b], h);
+      h = __ffma2_rn(bc2(e.y), w[b], h);
+    }
+    acc[a] = __ffma2_rn(bc2(sgn), h, acc[a]);
+  }
 }
 
-template <int RECON, int EPI, int SL>
-__global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
+// acc += sgn U^dag v
+__device__ __forceinline__ void mvdag_x2(const float2 *u, int ls, const float2 (&v)[3], float sgn, float2 (&acc)[3]) {
+  float2 w[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) w[b] = make_float2(v[b].y, -v[b].x);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2 e = u[(3 * b + a) * ls];
+      h = __ffma2_rn(bc2(e.x), v[b], h);
+      h = __ffma2_rn(bc2(e.y), w[b], h);
+    }
+    acc[a] = __ffma2_rn(bc2(sgn), h, acc[a]);
+  }
+}
+
+// the three colours of site s of system k (FP32 vector, read-only path)
+__device__ __forceinline__ void ld3(const VecArg &f, int k, int s, int Ve, float2 (&v)[3]) {
+  const float2 *p = reinterpret_cast<const float2 *>(f.v) + (long long)k * f.sstr + s;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = __ldg(p + (long long)c * Ve);
+}
+__device__ __forceinline__ void ld3_rw(const VecArg &f, int k, int s, int Ve, float2 (&v)[3]) {
+  const float2 *p = reinterpret_cast<const float2 *>(f.v) + (long long)k * f.sstr + s;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = p[(long long)c * Ve];
+}
+__device__ __forceinline__ void st3(const VecArg &f, int k, int s, int Ve, const float2 (&v)[3]) {
+  float2 *p = reinterpret_cast<float2 *>(f.v) + (long long)k * f.sstr + s;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) p[(long long)c * Ve] = v[c];
+}
+
+// per-system scalars of a launch, converted once per block
+struct SysF {
+  float alpha, beta, m4;
+  int act;
+};
+
+// dynamic shared memory: STG stages of one tile's stored links, plus the full
+// 3x3 copy the compute reads (reconstruct-12, or every single-stage form)
+inline unsigned nrhs_smem_bytes(int recon, int stg) {
+  const unsigned tile = 8u * (recon ? 6u : 9u) * (unsigned)LT * 8u, full = 8u * 9u * (unsigned)LT * 8u;
+  return (unsigned)stg * tile + ((recon || stg == 1) ? full : 0u);
+}
+
+// STG = 2: two stages, the next tile's copy in flight during the whole round
+// (2 blocks per SM); STG = 1: one stage, refilled as soon as this round's
+// links are in the full copy (less shared memory: 3 blocks per SM)
+template <int RECON, int EPI, int SL, int STG>
+__global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsArgs a) {
   static_assert(EPI == EPI_CG_K1R || EPI == EPI_CG_K2, "the two CG kernels");
+  static_assert(STG == 1 || STG == 2, "one or two stages");
   constexpr int BT = LT * SL;
   constexpr int NW = BT / 32;
   constexpr int NEL = RECON ? 6 : 9;
   constexpr int NV = (EPI == EPI_CG_K2) ? 2 : 1;
+  constexpr bool EXPAND = RECON || STG == 1;  // the compute reads the full copy
   constexpr unsigned TILE = 8u * NEL * LT * 8u;  // bytes of one tile's stored links
   extern __shared__ __align__(128) unsigned char smem[];
   float2 *stage0 = reinterpret_cast<float2 *>(smem);
-  float2 *full = reinterpret_cast<float2 *>(smem + 2 * TILE);  // [slot][9][LT] (reconstruct-12)
+  float2 *full = reinterpret_cast<float2 *>(smem + STG * TILE);  // [slot][9][LT]
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ volatile int failed;
-  __shared__ SysState sst[NRHS_MAX];
+  __shared__ SysF sf32[NRHS_MAX];
   __shared__ float red[NRHS_MAX][NW][NV];
   const Geom g = a.g;
   const int Ve = g.Ve, P = a.par_out, nsys = a.nsys;
@@ -53,10 +126,11 @@ __global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
   const int ntile = (Ve + LT - 1) / LT;
   const int nmine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   int issued = 0;  // thread 0: tiles whose copy was issued
+  // tile q goes to stage q % STG; its barrier completes phase q / STG when it lands
   auto issue = [&](int q) {
     const int t = (int)blockIdx.x + q * (int)gridDim.x;
     const float2 *src = reinterpret_cast<const float2 *>(a.links_tile) + ((long long)P * a.ntile + t) * (8 * NEL * LT);
-    bulk_copy_g2s(smem + (q & 1) * TILE, src, TILE, &bar[q & 1]);
+    bulk_copy_g2s(smem + (q % STG) * TILE, src, TILE, &bar[q % STG]);
     issued = q + 1;
   };
   grid_dep_trigger();
@@ -69,46 +143,61 @@ __global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
   __syncthreads();
   if (tid == 0 && nmine > 0) issue(0);  // the links never change during a solve
   grid_dep_wait();
-  for (int j = tid; j < nsys; j += BT) sst[j] = a.ctl.st[j];
+  for (int j = tid; j < nsys; j += BT) {
+    const SysState S = a.ctl.st[j];
+    SysF f;
+    f.alpha = (float)S.alpha;
+    f.beta = (float)S.beta;
+    f.m4 = (float)S.m4;
+    f.act = (a.gate == GATE_NONE || state_gate(S, a.gate)) ? 1 : 0;
+    sf32[j] = f;
+  }
   for (int k = tid; k < NRHS_MAX * NW * NV; k += BT) (&red[0][0][0])[k] = 0.f;
   if (tid == 0 && a.ctl.flags != nullptr && *(volatile int *)(a.ctl.flags + 4) != 0) failed = 1;
   __syncthreads();
 
   for (int round = 0; round < nmine; ++round) {
     const int t = (int)blockIdx.x + round * (int)gridDim.x;
-    const float2 *stg = stage0 + (round & 1) * (TILE / 8);
-    if (!failed && !mbar_wait(&bar[round & 1], (unsigned)(round >> 1) & 1u)) {
+    const float2 *stg = stage0 + (round % STG) * (TILE / 8);
+    if (!failed && !mbar_wait(&bar[round % STG], (unsigned)(round / STG) & 1u)) {
       failed = 1;
       if (a.ctl.flags != nullptr) atomicExch(a.ctl.flags + 4, 1);
     }
     const float2 *L = stg;
-    constexpr int LNE = RECON ? 9 : NEL;  // elements per link in the copy the compute reads
-    if (RECON) {
+    constexpr int LNE = EXPAND ? 9 : NEL;  // elements per link in the copy the compute reads
+    if (EXPAND) {
       __syncthreads();  // every thread is done with last round's full copy
-      // rebuild: 8 LT links, row 2 = conj(row0 x row1)
+      // the full copy: stored elements, and (reconstruct-12) row 2 = conj(row0 x row1)
       for (int k = tid; k < 8 * LT; k += BT) {
         const int slot = k / LT, ii = k % LT;
         const float2 *sp = stg + slot * (NEL * LT) + ii;
         float2 *dp = full + slot * (9 * LT) + ii;
-        float2 r0[3], r1[3];
+        if (RECON) {
+          float2 r0[3], r1[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          r0[c] = sp[c * LT];
-          r1[c] = sp[(3 + c) * LT];
-          dp[c * LT] = r0[c];
-          dp[(3 + c) * LT] = r1[c];
-        }
+          for (int c = 0; c < 3; ++c) {
+            r0[c] = sp[c * LT];
+            r1[c] = sp[(3 + c) * LT];
+            dp[c * LT] = r0[c];
+            dp[(3 + c) * LT] = r1[c];
+          }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-          const float re = (r0[c1].x * r1[c2].x - r0[c1].y * r1[c2].y) - (r0[c2].x * r1[c1].x - r0[c2].y * r1[c1].y);
-          const float im = (r0[c1].x * r1[c2].y + r0[c1].y * r1[c2].x) - (r0[c2].x * r1[c1].y + r0[c2].y * r1[c1].x);
-          dp[(6 + c) * LT] = make_float2(re, -im);
+          for (int c = 0; c < 3; ++c) {
+            const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            const float re =
+                (r0[c1].x * r1[c2].x - r0[c1].y * r1[c2].y) - (r0[c2].x * r1[c1].x - r0[c2].y * r1[c1].y);
+            const float im =
+                (r0[c1].x * r1[c2].y + r0[c1].y * r1[c2].x) - (r0[c2].x * r1[c1].y + r0[c2].y * r1[c1].x);
+            dp[(6 + c) * LT] = make_float2(re, -im);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 9; ++e) dp[e * LT] = sp[e * LT];
         }
       }
       L = full;
     }
-    __syncthreads();  // this round's links ready; last round's stage free
+    __syncthreads();  // this round's links ready; the stage the next copy fills is free
     if (tid == 0 && !failed && round + 1 < nmine) {
       fence_proxy_async_smem();
       issue(round + 1);
@@ -144,55 +233,52 @@ __global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
       }
     }
     for (int j = lane; j < nsys; j += SL) {
-      const SysState &S = sst[j];
-      if (!(a.gate == GATE_NONE || state_gate(S, a.gate))) continue;  // uniform per warp
-      const float beta = (float)S.beta, alpha = (float)S.alpha, m4 = (float)S.m4;
+      const SysF S = sf32[j];
+      if (!S.act) continue;  // uniform per warp
+      const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
       float q0 = 0.f, q1 = 0.f;
       if (valid) {
-        float vf[4][6], vb[4][6], c0[6], c1[6], c2[6];
+        float2 vf[4][3], vb[4][3], c0[3], c1[3], c2[3];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-          load_vec<P32>(a.in, j, sf[mu], Ve, vf[mu]);
-          load_vec<P32>(a.in, j, sb[mu], Ve, vb[mu]);
+          ld3(a.in, j, sf[mu], Ve, vf[mu]);
+          ld3(a.in, j, sb[mu], Ve, vb[mu]);
         }
         if (EPI == EPI_CG_K2) {
-          load_vec_rw<P32>(a.center, j, s, Ve, c0);
-          load_vec_rw<P32>(a.aux, j, s, Ve, c1);
-          load_vec_rw<P32>(a.xlo, j, s, Ve, c2);
+          ld3_rw(a.center, j, s, Ve, c0);
+          ld3_rw(a.aux, j, s, Ve, c1);
+          ld3_rw(a.xlo, j, s, Ve, c2);
         } else {
-          load_vec_rw<P32>(a.out, j, s, Ve, c0);
+          ld3_rw(a.out, j, s, Ve, c0);
         }
-        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-          float u[18];
-          load_link_at<P32, 0, true>(L + mu * (LNE * LT) + i, LT, u);
-          mv_acc(u, vf[mu], bf[mu], acc);
-          load_link_at<P32, 0, true>(L + (4 + mu) * (LNE * LT) + i, LT, u);
-          mvdag_acc(u, vb[mu], -bb[mu], acc);
+          mv_x2(L + mu * (LNE * LT) + i, LT, vf[mu], bf[mu], acc);
+          mvdag_x2(L + (4 + mu) * (LNE * LT) + i, LT, vb[mu], -bb[mu], acc);
         }
         if (EPI == EPI_CG_K2) {
           // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            c0[k] = c1[k] + beta * c0[k];
-            const float ap = m4 * c0[k] - acc[k];
-            c1[k] -= alpha * ap;
-            c2[k] += alpha * c0[k];
-            q0 += c1[k] * c1[k];
-            q1 += c1[k] * c0[k];
+          for (int k = 0; k < 3; ++k) {
+            c0[k] = __ffma2_rn(bc2(beta), c0[k], c1[k]);
+            const float2 ap = __ffma2_rn(bc2(m4), c0[k], make_float2(-acc[k].x, -acc[k].y));
+            c1[k] = __ffma2_rn(bc2(-alpha), ap, c1[k]);
+            c2[k] = __ffma2_rn(bc2(alpha), c0[k], c2[k]);
+            q0 += c1[k].x * c1[k].x + c1[k].y * c1[k].y;
+            q1 += c1[k].x * c0[k].x + c1[k].y * c0[k].y;
           }
-          store_vec<P32>(a.center, j, s, Ve, c0);
-          store_vec<P32>(a.aux, j, s, Ve, c1);
-          store_vec<P32>(a.xlo, j, s, Ve, c2);
+          st3(a.center, j, s, Ve, c0);
+          st3(a.aux, j, s, Ve, c1);
+          st3(a.xlo, j, s, Ve, c2);
         } else {
           // t = D_oe r + beta t_old
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            c0[k] = acc[k] + beta * c0[k];
-            q0 += c0[k] * c0[k];
+          for (int k = 0; k < 3; ++k) {
+            c0[k] = __ffma2_rn(bc2(beta), c0[k], acc[k]);
+            q0 += c0[k].x * c0[k].x + c0[k].y * c0[k].y;
           }
-          store_vec<P32>(a.out, j, s, Ve, c0);
+          st3(a.out, j, s, Ve, c0);
         }
       }
       q0 = warp_sum(q0);
@@ -207,7 +293,7 @@ __global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
   if (failed) {
     // the copies still outstanding land before the block exits (bounded)
     if (tid == 0)
-      for (int q = issued - 2 > 0 ? issued - 2 : 0; q < issued; ++q) mbar_wait(&bar[q & 1], (unsigned)(q >> 1) & 1u);
+      for (int q = issued - STG > 0 ? issued - STG : 0; q < issued; ++q) mbar_wait(&bar[q % STG], (unsigned)(q / STG) & 1u);
     __syncthreads();
   }
   // one FP64 partial per system and value: the warps of the system's lane in order
@@ -222,10 +308,10 @@ __global__ void __launch_bounds__(LT * SL, 2) k_cg_nrhs(const DsArgs a) {
   }
 }
 
-template <int RC_, int EPI_, int SL_>
+template <int RC_, int EPI_, int SL_, int STG_>
 static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **kptr) {
-  auto k = k_cg_nrhs<RC_, EPI_, SL_>;
-  const unsigned smem = nrhs_smem_bytes(RC_);
+  auto k = k_cg_nrhs<RC_, EPI_, SL_, STG_>;
+  const unsigned smem = nrhs_smem_bytes(RC_, STG_);
   static bool attr_set = false;  // benign race: setting it twice is harmless
   if (!attr_set) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -239,16 +325,18 @@ static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const
   return launch_ex_full(k, nblocks, LT * SL_, smem, st, a.pdl != 0, a.l2_base, a.l2_bytes, a.l2_hit, a);
 }
 
-cudaError_t launch_cg_nrhs(int recon, int sl, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
+cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr) {
-#define STAG_NR(RC_, EPI_, SL_) \
-  if (recon == RC_ && EPI == EPI_ && sl == SL_) return nrhs_one<RC_, EPI_, SL_>(nblocks, st, a, kptr);
-  STAG_NR(0, EPI_CG_K1R, 2) STAG_NR(0, EPI_CG_K2, 2) STAG_NR(1, EPI_CG_K1R, 2) STAG_NR(1, EPI_CG_K2, 2)
-  STAG_NR(0, EPI_CG_K1R, 4) STAG_NR(0, EPI_CG_K2, 4) STAG_NR(1, EPI_CG_K1R, 4) STAG_NR(1, EPI_CG_K2, 4)
+#define STAG_NR(RC_, EPI_, SL_, STG_)                   \
+  if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + SL_) \
+    return nrhs_one<RC_, EPI_, SL_, STG_>(nblocks, st, a, kptr);
+  STAG_NR(0, EPI_CG_K1R, 2, 2) STAG_NR(0, EPI_CG_K2, 2, 2) STAG_NR(1, EPI_CG_K1R, 2, 2) STAG_NR(1, EPI_CG_K2, 2, 2)
+  STAG_NR(0, EPI_CG_K1R, 4, 2) STAG_NR(0, EPI_CG_K2, 4, 2) STAG_NR(1, EPI_CG_K1R, 4, 2) STAG_NR(1, EPI_CG_K2, 4, 2)
+  STAG_NR(1, EPI_CG_K1R, 4, 1) STAG_NR(1, EPI_CG_K2, 4, 1) STAG_NR(0, EPI_CG_K1R, 4, 1) STAG_NR(0, EPI_CG_K2, 4, 1)
 #undef STAG_NR
   return cudaErrorNotSupported;
 }
 
-unsigned cg_nrhs_smem(int recon) { return nrhs_smem_bytes(recon); }
+unsigned cg_nrhs_smem(int recon, int form) { return nrhs_smem_bytes(recon, form >= 10 ? 1 : 2); }
 
 }  // namespace stag
