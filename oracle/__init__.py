@@ -75,6 +75,9 @@ def _bind(path):
         "orc_set_threads": (None, [I]),
         "orc_su3_project": (None, [P, P]),
         "orc_hyp": (None, [P, P, P, P]),
+        "orc_spin_taste": (None, [I, I, P]),
+        "orc_hypercube_path": (None, [P, P, P, I, I, P]),
+        "orc_npr_contract": (None, [P, P, I, I, I, I, P, P, P, P, P]),
         "orc_threads": (I, []),
     }
     for name, (res, args) in sig.items():
@@ -287,6 +290,31 @@ def hyp(L, links, alpha=HYP_ALPHA):
     a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
     out = np.empty_like(U)
     lib.orc_hyp(_p(d), _p(U), _p(a), _p(out))
+    return out
+
+
+def spin_taste(S, F):
+    """16 x 16 complex matrix (g_S x x_F)_AB = Tr(g_A^dag g_S g_B g_F^dag) / 4 (4-bit S, F)."""
+    out = np.empty((16, 16), np.complex128)
+    _load().orc_spin_taste(int(S), int(F), _p(out))
+    return out
+
+
+def hypercube_path(L, links, zc, A, D):
+    """Average over the shortest paths from corner A to corner D of hypercube zc of the link products."""
+    W = np.empty((3, 3), np.complex128)
+    z = np.ascontiguousarray(np.asarray(zc, dtype=np.int32))
+    _load().orc_hypercube_path(_p(_dims(L)), _p(_c128(links)), _p(z), int(A), int(D), _p(W))
+    return W
+
+
+def npr_contract(L, links, S1, F1, S2, F2, chibar1, chi2, chibar3, chi4):
+    """O(z) of every hypercube ([V/16] complex) of the one-colour-trace four-fermion contraction."""
+    V = volume(L)
+    out = np.empty(V // 16, np.complex128)
+    f = [_c128(v) for v in (chibar1, chi2, chibar3, chi4)]
+    _load().orc_npr_contract(_p(_dims(L)), _p(_c128(links)), int(S1), int(F1), int(S2), int(F2),
+                             _p(f[0]), _p(f[1]), _p(f[2]), _p(f[3]), _p(out))
     return out
 
 

@@ -775,3 +775,209 @@ void orc_hyp(const int L[4], const double *Ud, const double *alpha, double *outd
     free(Vb);
     free(Vt);
 }
+
+/* ------------------------------------------------------------------ */
+/* NPR: the one-colour-trace four-fermion contraction                  */
+/* ------------------------------------------------------------------ */
+/*
+ * Sec. 4 of the paper (its DP workload, Eq. (ffop)): on every hypercube z of
+ * the lattice (sites z_A = 2z + A, corners A in {0,1}^4),
+ *   O(z) = sum_{A,B,C,D} [chibar1(z_A) (g_S1 x x_F1)_AB chi2(z_B)]
+ *                        [chibar3(z_C) (g_S2 x x_F2)_CD chi4(z_D)]
+ *                        [U_AD(z)]_{c1 c4} [U_CB(z)]_{c3 c2},
+ * colour c1 of chibar1 tied to c4 of chi4 and c3 of chibar3 to c2 of chi2
+ * through the links (one colour trace across the two bilinears).  The paper
+ * writes the form only; the readings (recorded with the design notes):
+ *   - spin-taste matrices (g_S x x_F)_AB = (1/4) Tr(g_A^dag g_S g_B g_F^dag),
+ *     g_A = g_1^A1 g_2^A2 g_3^A3 g_4^A4 with Euclidean Hermitian gammas
+ *     (directions x, y, z, t = bits 0..3 of A), here from explicit 4x4
+ *     matrices (the chiral basis);
+ *   - U_AD(z) = the average over the |A xor D|! shortest lattice paths from
+ *     z_A to z_D (inside the hypercube) of the products of links along them
+ *     (U_mu(y) for a step +mu, U_mu(y - mu)^dag for -mu), 1 for A = D;
+ *   - chibar1, chi2, chibar3, chi4: colour-vector fields [V][3] (for NPR the
+ *     columns of quark propagators); no conjugation (chibar is its own field).
+ * O has [V/16] entries, hypercube index h = z0 + (L0/2)(z1 + (L1/2)(z2 + (L2/2) z3)).
+ */
+
+/* Euclidean Hermitian gamma matrices, chiral basis: g_k = [[0, -i s_k], [i s_k, 0]], g_4 = [[0, 1], [1, 0]] */
+static void gamma_mat(int mu, cplx g[16])
+{
+    static const double sig[3][2][2][2] = {
+        {{{0, 0}, {1, 0}}, {{1, 0}, {0, 0}}},
+        {{{0, 0}, {0, -1}}, {{0, 1}, {0, 0}}},
+        {{{1, 0}, {0, 0}}, {{0, 0}, {-1, 0}}},
+    };
+    for (int k = 0; k < 16; ++k) g[k].re = g[k].im = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            if (mu < 3) {
+                cplx s = {sig[mu][a][b][0], sig[mu][a][b][1]};
+                cplx mi = {0, -1}, pi = {0, 1};
+                g[a * 4 + (2 + b)] = c_mul(mi, s);     /* upper right: -i s */
+                g[(2 + a) * 4 + b] = c_mul(pi, s);     /* lower left:  +i s */
+            } else if (a == b) {
+                g[a * 4 + (2 + b)].re = 1.0;
+                g[(2 + a) * 4 + b].re = 1.0;
+            }
+        }
+}
+
+static void m4_mul(const cplx *a, const cplx *b, cplx *c)
+{
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            cplx s = {0, 0};
+            for (int k = 0; k < 4; ++k) s = c_add(s, c_mul(a[i * 4 + k], b[k * 4 + j]));
+            c[i * 4 + j] = s;
+        }
+}
+
+/* g_A for a 4-bit corner A */
+static void gamma_of(int A, cplx g[16])
+{
+    for (int k = 0; k < 16; ++k) { g[k].re = (k % 5 == 0) ? 1.0 : 0.0; g[k].im = 0.0; }
+    for (int mu = 0; mu < 4; ++mu) {
+        if (!((A >> mu) & 1)) continue;
+        cplx gm[16], t[16];
+        gamma_mat(mu, gm);
+        m4_mul(g, gm, t);
+        for (int k = 0; k < 16; ++k) g[k] = t[k];
+    }
+}
+
+/* out[A*16+B] = (1/4) Tr(g_A^dag g_S g_B g_F^dag) (complex) */
+void orc_spin_taste(int S, int F, double *outd)
+{
+    cplx *out = (cplx *)outd;
+    cplx gS[16], gF[16], gFd[16];
+    gamma_of(S, gS);
+    gamma_of(F, gF);
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) gFd[i * 4 + j] = c_conj(gF[j * 4 + i]);
+    for (int A = 0; A < 16; ++A) {
+        cplx gA[16], gAd[16];
+        gamma_of(A, gA);
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) gAd[i * 4 + j] = c_conj(gA[j * 4 + i]);
+        for (int B = 0; B < 16; ++B) {
+            cplx gB[16], t1[16], t2[16], t3[16];
+            gamma_of(B, gB);
+            m4_mul(gAd, gS, t1);
+            m4_mul(t1, gB, t2);
+            m4_mul(t2, gFd, t3);
+            cplx tr = {0, 0};
+            for (int k = 0; k < 4; ++k) tr = c_add(tr, t3[k * 5]);
+            out[A * 16 + B] = c_scale(0.25, tr);
+        }
+    }
+}
+
+/* site of corner A of hypercube with coordinates zc */
+static long corner_site(const int L[4], const int zc[4], int A)
+{
+    int x[4];
+    for (int mu = 0; mu < 4; ++mu) x[mu] = 2 * zc[mu] + ((A >> mu) & 1);
+    return lex_of(L, x);
+}
+
+/* W = average over the shortest paths from corner A to corner D of hypercube zc */
+void orc_hypercube_path(const int L[4], const double *Ud, const int zc[4], int A, int D, double *Wd)
+{
+    const cplx *U = (const cplx *)Ud;
+    cplx *W = (cplx *)Wd;
+    long V = volume(L);
+    int dirs[4], n = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        if (((A ^ D) >> mu) & 1) dirs[n++] = mu;
+    for (int k = 0; k < 9; ++k) { W[k].re = (k % 4 == 0) ? 1.0 : 0.0; W[k].im = 0.0; }
+    if (n == 0) return;
+    for (int k = 0; k < 9; ++k) W[k].re = W[k].im = 0.0;
+    /* every ordering of the differing directions (permutations by Heap's enumeration over indices) */
+    int perm[4] = {0, 1, 2, 3};
+    int npaths = 0;
+    /* enumerate all n! orderings with a plain nested loop over permutations of 0..n-1 */
+    int idx[4];
+    int total = 1;
+    for (int k = 2; k <= n; ++k) total *= k;
+    for (int p = 0; p < total; ++p) {
+        /* p-th permutation in factorial numbering */
+        int avail[4] = {0, 1, 2, 3}, m = n, r = p;
+        for (int k = 0; k < n; ++k) {
+            int f = 1;
+            for (int q = 2; q <= m - 1; ++q) f *= q;
+            int sel = r / f;
+            r %= f;
+            idx[k] = avail[sel];
+            for (int q = sel; q < m - 1; ++q) avail[q] = avail[q + 1];
+            --m;
+        }
+        cplx P[9];
+        for (int k = 0; k < 9; ++k) { P[k].re = (k % 4 == 0) ? 1.0 : 0.0; P[k].im = 0.0; }
+        int cur = A;
+        for (int k = 0; k < n; ++k) {
+            int mu = dirs[idx[k]];
+            int nxt = cur ^ (1 << mu);
+            cplx step[9], T[9];
+            if ((cur >> mu) & 1) { /* step -mu: U_mu(z_nxt)^dag */
+                m_dag(U + ((long)mu * V + corner_site(L, zc, nxt)) * 9, step);
+            } else {                /* step +mu: U_mu(z_cur) */
+                for (int q = 0; q < 9; ++q) step[q] = U[((long)mu * V + corner_site(L, zc, cur)) * 9 + q];
+            }
+            m_mul(P, step, T);
+            for (int q = 0; q < 9; ++q) P[q] = T[q];
+            cur = nxt;
+        }
+        for (int q = 0; q < 9; ++q) W[q] = c_add(W[q], P[q]);
+        ++npaths;
+    }
+    (void)perm;
+    for (int q = 0; q < 9; ++q) W[q] = c_scale(1.0 / npaths, W[q]);
+}
+
+/* O(z) for every hypercube (out [V/16] complex); returns nothing */
+void orc_npr_contract(const int L[4], const double *Ud, int S1, int F1, int S2, int F2, const double *chibar1d,
+                      const double *chi2d, const double *chibar3d, const double *chi4d, double *outd)
+{
+    const cplx *cb1 = (const cplx *)chibar1d, *c2 = (const cplx *)chi2d;
+    const cplx *cb3 = (const cplx *)chibar3d, *c4 = (const cplx *)chi4d;
+    cplx *out = (cplx *)outd;
+    cplx st1[256], st2[256];
+    orc_spin_taste(S1, F1, (double *)st1);
+    orc_spin_taste(S2, F2, (double *)st2);
+    int H[4] = {L[0] / 2, L[1] / 2, L[2] / 2, L[3] / 2};
+    long nh = (long)H[0] * H[1] * H[2] * H[3];
+    for (long h = 0; h < nh; ++h) {
+        int zc[4];
+        long r = h;
+        zc[0] = (int)(r % H[0]); r /= H[0];
+        zc[1] = (int)(r % H[1]); r /= H[1];
+        zc[2] = (int)(r % H[2]);
+        zc[3] = (int)(r / H[2]);
+        cplx o = {0, 0};
+        for (int A = 0; A < 16; ++A)
+            for (int B = 0; B < 16; ++B) {
+                cplx s1 = st1[A * 16 + B];
+                if (s1.re == 0.0 && s1.im == 0.0) continue;
+                for (int C = 0; C < 16; ++C)
+                    for (int D = 0; D < 16; ++D) {
+                        cplx s2 = st2[C * 16 + D];
+                        if (s2.re == 0.0 && s2.im == 0.0) continue;
+                        cplx Wad[9], Wcb[9];
+                        orc_hypercube_path(L, Ud, zc, A, D, (double *)Wad);
+                        orc_hypercube_path(L, Ud, zc, C, B, (double *)Wcb);
+                        long sA = corner_site(L, zc, A), sB = corner_site(L, zc, B);
+                        long sC = corner_site(L, zc, C), sD = corner_site(L, zc, D);
+                        /* chibar1_c1 U_AD[c1][c4] chi4_c4 and chibar3_c3 U_CB[c3][c2] chi2_c2 */
+                        cplx t1 = {0, 0}, t2 = {0, 0};
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) {
+                                t1 = c_add(t1, c_mul(cb1[sA * 3 + a], c_mul(Wad[a * 3 + b], c4[sD * 3 + b])));
+                                t2 = c_add(t2, c_mul(cb3[sC * 3 + a], c_mul(Wcb[a * 3 + b], c2[sB * 3 + b])));
+                            }
+                        o = c_add(o, c_mul(c_mul(s1, s2), c_mul(t1, t2)));
+                    }
+            }
+        out[h] = o;
+    }
+}

@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_hyp as hy
+from tests import test_oracle_npr as npr
 from tests import test_oracle_operator as op
 from tests import test_oracle_solver as sv
 
@@ -77,6 +78,20 @@ MUTANTS = {
         "fctx side = {Vt, V, L, mu}, mid = {Vt, V, L, nu};", "fctx side = {Vt, V, L, nu}, mid = {Vt, V, L, nu};"),
     "projection keeps the determinant phase": (
         "for (int k = 0; k < 9; ++k) W[k] = c_mul(Y[k], rot);", "for (int k = 0; k < 9; ++k) W[k] = Y[k];"),
+    "NPR: g_A not daggered": (
+        "for (int j = 0; j < 4; ++j) gAd[i * 4 + j] = c_conj(gA[j * 4 + i]);",
+        "for (int j = 0; j < 4; ++j) gAd[i * 4 + j] = gA[i * 4 + j];"),
+    "NPR: taste matrix not daggered": (
+        "for (int j = 0; j < 4; ++j) gFd[i * 4 + j] = c_conj(gF[j * 4 + i]);",
+        "for (int j = 0; j < 4; ++j) gFd[i * 4 + j] = gF[i * 4 + j];"),
+    "NPR: backward path step not daggered": (
+        "m_dag(U + ((long)mu * V + corner_site(L, zc, nxt)) * 9, step);",
+        "for (int q = 0; q < 9; ++q) step[q] = U[((long)mu * V + corner_site(L, zc, nxt)) * 9 + q];"),
+    "NPR: colours of the two bilinears not crossed": (
+        "t2 = c_add(t2, c_mul(cb3[sC * 3 + a], c_mul(Wcb[a * 3 + b], c2[sB * 3 + b])));",
+        "t2 = c_add(t2, c_mul(cb3[sC * 3 + b], c_mul(Wcb[a * 3 + b], c2[sB * 3 + a])));"),
+    "NPR: path from D to A": (
+        "orc_hypercube_path(L, Ud, zc, A, D, (double *)Wad);", "orc_hypercube_path(L, Ud, zc, D, A, (double *)Wad);"),
     "multi-mass oracle reuses the first mass": (
         "int st = orc_cg(L, antiperiodic, U, masses[k], b, x + k * n, tol, maxiter,",
         "int st = orc_cg(L, antiperiodic, U, masses[0], b, x + k * n, tol, maxiter,"),
@@ -101,6 +116,11 @@ def _pins():
     for d in range(4):
         yield lambda d=d: hy.test_translation_invariance(d)
     yield hy.test_first_order_response_by_path_counting
+    yield npr.test_spin_taste_identity_phases_and_orthogonality
+    yield npr.test_hypercube_paths
+    yield lambda: npr.test_contraction_gauge_invariance((7, 3, 2, 12))
+    yield npr.test_contraction_translation_by_one_hypercube
+    yield npr.test_contraction_unit_links_closed_form
 
 
 @pytest.fixture(scope="module")
