@@ -158,6 +158,31 @@ int stag_cg_solve(stag_ctx *ctx, const double *const src[], int nrhs, const doub
                   int iters[], double true_res[]);
 
 /*
+ * The one-colour-trace four-fermion contraction of the NPR (RI-MOM) workload
+ * (Sec. 4, Eq. (ffop): FP64, 97 % of that code's time), on every hypercube z
+ * of the lattice (sites z_A = 2z + A, corners A in {0,1}^4):
+ *   O(z) = sum_{A,B,C,D} [chibar1(z_A) (g_S1 x x_F1)_AB chi2(z_B)]
+ *                        [chibar3(z_C) (g_S2 x x_F2)_CD chi4(z_D)]
+ *                        [U_AD(z)]_{c1 c4} [U_CB(z)]_{c3 c2}
+ * (colour c1 of chibar1 tied to c4 of chi4 and c3 of chibar3 to c2 of chi2
+ * through the links), with the readings the paper leaves open:
+ *   (g_S x x_F)_AB = (1/4) Tr(g_A^dag g_S g_B g_F^dag), g_A = g_1^A1 g_2^A2
+ *   g_3^A3 g_4^A4 (Euclidean Hermitian gammas; bit mu of A = direction mu of
+ *   x, y, z, t); U_AD(z) = the average over the shortest lattice paths from
+ *   z_A to z_D of the link products (U_mu for a step +mu, U_mu^dag for -mu).
+ *   spin_taste  (S1, F1, S2, F2), each a 4-bit corner mask 0..15;
+ *   chibar1, chi2, chibar3, chi4  [V][3][2] FP64 colour-vector fields in the
+ *               links' lexicographic site order (for NPR: propagator columns),
+ *               host or device;
+ *   O_hyp       [V/16][2] (may be NULL): O(z) at hypercube index
+ *               z0 + (Lx/2)(z1 + (Ly/2)(z2 + (Lz/2) z3)), host or device;
+ *   O_sum       [2] (may be NULL): sum over z, fixed-order FP64 reduction.
+ * Uses the uploaded gauge field (FP64).  Errors: STAG_ERR_ARG, _STATE, _CUDA.
+ */
+int stag_npr_contract(stag_ctx *ctx, const int spin_taste[4], const double *chibar1, const double *chi2,
+                      const double *chibar3, const double *chi4, double *O_hyp, double *O_sum);
+
+/*
  * HYP smearing of a gauge field (Sec. 3: the quarks are "HYP-smeared"
  * staggered quarks; the paper gives no parameters): links_out = the
  * hypercubic-blocked field of links_in by Hasenfratz and Knechtli's three

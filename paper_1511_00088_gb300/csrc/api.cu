@@ -203,6 +203,7 @@ struct stag_ctx {
   VecBuf full_e, full_o, full_x;  // full-lattice solve: halves of the sources, odd half of a solution
   DevBuf red;                     // block sums of the action's reduction
   DevBuf hyp_b, hyp_t, hyp_io;    // HYP smearing: the two decorated levels, host staging
+  DevBuf npr_f, npr_o;            // NPR contraction: staged fields, per-hypercube values and their sum
   VecBuf ms_p, ms_x;              // multi-shift CG: shifted directions and solutions (FP32)
   DevBuf ms_sh;                   // their ShiftState
   PinnedBuf ms_h;
@@ -2073,6 +2074,43 @@ int stag_cg_solve(stag_ctx *c, const double *const src[], int nrhs, const double
     if (!std::isfinite(masses[k])) return arg_err(c, "non-finite mass");
   CK(cudaSetDevice(c->device));
   return solve_impl(c, src, nrhs, masses, nmass, tol, maxiter, precision, x, iters, true_res);
+}
+
+int stag_npr_contract(stag_ctx *c, const int spin_taste[4], const double *chibar1, const double *chi2,
+                      const double *chibar3, const double *chi4, double *O_hyp, double *O_sum) {
+  if (!c) return STAG_ERR_ARG;
+  if (!spin_taste || !chibar1 || !chi2 || !chibar3 || !chi4 || (!O_hyp && !O_sum))
+    return arg_err(c, "NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (spin_taste[k] < 0 || spin_taste[k] > 15) return arg_err(c, "spin/taste masks are 4-bit (0..15)");
+  CK(cudaSetDevice(c->device));
+  if (!c->have_links) {
+    c->err = "no gauge field: call stag_links_upload first";
+    return STAG_ERR_STATE;
+  }
+  const size_t fb = sizeof(double) * 6ull * (size_t)c->V;
+  const long long nh = c->V / 16;
+  const double *f[4] = {chibar1, chi2, chibar3, chi4};
+  const double2 *d[4];
+  CK(c->npr_f.ensure(4 * fb));
+  for (int k = 0; k < 4; ++k) {
+    if (is_device_ptr(f[k])) {
+      d[k] = reinterpret_cast<const double2 *>(f[k]);
+    } else {
+      CK(cudaMemcpyAsync((char *)c->npr_f.p + k * fb, f[k], fb, cudaMemcpyHostToDevice, c->stream));
+      d[k] = reinterpret_cast<const double2 *>((char *)c->npr_f.p + k * fb);
+    }
+  }
+  CK(c->npr_o.ensure(sizeof(double2) * (size_t)(nh + 1)));
+  double2 *out = (O_hyp && is_device_ptr(O_hyp)) ? reinterpret_cast<double2 *>(O_hyp) : (double2 *)c->npr_o.p;
+  double2 *sum = (double2 *)c->npr_o.p + nh;
+  CK(launch_npr(c->dims, reinterpret_cast<const double2 *>(c->links_canon.p), spin_taste, d[0], d[1], d[2], d[3],
+                out, O_sum ? sum : nullptr, c->stream));
+  if (O_hyp && out == (double2 *)c->npr_o.p)
+    CK(cudaMemcpyAsync(O_hyp, out, sizeof(double2) * (size_t)nh, cudaMemcpyDeviceToHost, c->stream));
+  if (O_sum) CK(cudaMemcpyAsync(O_sum, sum, sizeof(double2), cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return STAG_OK;
 }
 
 int stag_hyp_smear(stag_ctx *c, const double alpha[3], const double *links_in, double *links_out) {

@@ -126,6 +126,12 @@ cudaError_t launch_pack_links_tiled(int LP, int recon, const double2 *src, void 
 cudaError_t launch_su3_defect(const double2 *U, long long nlinks, unsigned long long *out,
                               cudaStream_t st);
 
+// NPR one-colour-trace four-fermion contraction (npr.cu): out[h] = O(z_h) for
+// every hypercube (V / 16 entries), *sum (may be null) = their sum; U the
+// canonical [4][V][3][3] links, fields [V][3]; st = (S1, F1, S2, F2), 4-bit corner masks
+cudaError_t launch_npr(const int dims[4], const double2 *U, const int st[4], const double2 *cb1, const double2 *c2,
+                       const double2 *cb3, const double2 *c4, double2 *out, double2 *sum, cudaStream_t s);
+
 // HYP smearing (hyp.cu): out [4][V][3][3] = the smeared links of U (same
 // layout; out may alias U); Vb, Vt scratch of 12 V links each; alpha = (a1, a2, a3)
 cudaError_t launch_hyp(const int dims[4], const double2 *U, const double alpha[3], double2 *Vb, double2 *Vt,

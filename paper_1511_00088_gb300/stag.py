@@ -82,6 +82,7 @@ def load():
             "stag_solve_full": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_cg_solve_multishift": (I, [P, PP, I, P, I, D, I, I, PP, P, P]),
             "stag_hyp_smear": (I, [P, P, P, P]),
+            "stag_npr_contract": (I, [P, P, P, P, P, P, P, P]),
             "stag_time_dslash": (I, [P, I, I, P, P]),
             "stag_time_cg_kernel": (I, [P, I, I, I, P, P]),
             "stag_solve_counters": (I, [P, P, P]),
@@ -175,6 +176,13 @@ def stag_cg_solve(ctx, srcs, masses, tol, maxiter, precision, xs, iters=None, tr
     st = lib.stag_cg_solve(ctx, sp, nrhs, m.ctypes.data, nmass, float(tol), int(maxiter),
                            int(precision), xp, it.ctypes.data, tr.ctypes.data)
     return st, it, tr
+
+
+def stag_npr_contract(ctx, spin_taste, chibar1, chi2, chibar3, chi4, O_hyp=None, O_sum=None):
+    """NPR contraction; spin_taste = (S1, F1, S2, F2); O_sum a complex128 array of one element."""
+    st = (ctypes.c_int * 4)(*[int(v) for v in spin_taste])
+    return load().stag_npr_contract(ctx, st, _ptr(chibar1), _ptr(chi2), _ptr(chibar3), _ptr(chi4),
+                                    None if O_hyp is None else _ptr(O_hyp), None if O_sum is None else _ptr(O_sum))
 
 
 def stag_hyp_smear(ctx, alpha, links_in, links_out):
@@ -400,6 +408,23 @@ class Context:
         ok = (STAG_OK, STAG_NOT_CONVERGED) if allow_not_converged else (STAG_OK,)
         self._check(st, ok)
         return xs, st, it, tr
+
+    def npr_contract(self, spin_taste, chibar1, chi2, chibar3, chi4):
+        """(O per hypercube (V/16,) complex128, their sum) of the one-colour-trace
+        four-fermion contraction on the uploaded links."""
+        try:
+            import torch
+            dev = chibar1.device if isinstance(chibar1, torch.Tensor) else None
+        except ImportError:  # pragma: no cover
+            dev = None
+        if dev is not None:
+            import torch
+            O = torch.empty(self.V // 16, dtype=torch.complex128, device=dev)
+        else:
+            O = np.empty(self.V // 16, np.complex128)
+        tot = np.zeros(1, np.complex128)
+        self._check(stag_npr_contract(self.h, spin_taste, chibar1, chi2, chibar3, chi4, O, tot))
+        return O, complex(tot[0])
 
     def hyp_smear(self, links, alpha=None, out=None):
         """HYP-smeared copy of links (4, V, 3, 3) complex128 (out may be links)."""
