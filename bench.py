@@ -504,9 +504,11 @@ def run_ours(args):
         updates.append(nu)
         res.append(tr)
         # one pack per source and mass, init + its finalize, one unpack per
-        # system; per loop pass 2 CG kernels per iteration and one finalize;
-        # per update step 5 kernels
-        launches += 2 * nsys + 2 + (2 * unroll + 1) * passes + 5 * ups
+        # system; per loop pass 2 CG kernels per iteration and one finalize
+        # (the multi-RHS form: a finalize after each CG kernel); per update
+        # step 5 kernels
+        per_pass = 4 * unroll if ctx.solve_form()["kernels"] == "k_cg_nrhs" else 2 * unroll + 1
+        launches += 2 * nsys + 2 + per_pass * passes + 5 * ups
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

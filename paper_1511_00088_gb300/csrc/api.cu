@@ -837,10 +837,11 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
     if (nrhs_ok && !(fns && fns[0] != 0) && !(fmr && fmr[0] != 0)) {
       cands.push_back(202);
       cands.push_back(204);
-      cands.push_back(214);
     }
     // STAG_NRHS = 2 or 4: this form with that many threads per site (two link
-    // stages), 14: 4 threads per site with one stage; 0: never this form
+    // stages), 14: 4 threads per site with one stage (3 blocks per SM; measured
+    // slower: 48-system 20^3 x 64 solve 3.34 s vs 2.36 s, so not a default
+    // candidate); 0: never this form
     const char *fnr = getenv("STAG_NRHS");
     if (fnr && nrhs_ok) {
       const int f = atoi(fnr);
