@@ -105,19 +105,21 @@ def test_half_storage_output_rounding(prec, L):
     assert rel(g, ref) < 2.0 ** -MANT[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_full_size_production_lattice(prec):
-    """20^3 x 64 (the paper's production shape), the launch configuration of
-    the benchmark: whole-field comparison with the oracle."""
+@pytest.mark.parametrize("prec,recon", [("fp64", False), ("fp32", False), ("fp32", True), ("fp16", False),
+                                        ("fp16", True), ("bf16", False), ("bf16", True)])
+def test_full_size_production_lattice(prec, recon):
+    """20^3 x 64 (the paper's production shape): whole-field comparison with the
+    oracle on the inputs as the GPU stores them, every link format (the
+    benchmark's FP32 reconstruct-12 included) and storage precision."""
     L = (20, 20, 20, 64)
     V = synth.volume(L)
     U = synth.random_links(L, 0.4, 1001)
     xe = synth.gaussian_vector(V // 2, 1002)
     m = 0.01
-    Ue = effective_links(U, prec, False)
+    Ue = effective_links(U, prec, recon)
     ref = oracle.mdagm(L, Ue, m, effective_vec(xe, prec))
     ref_oe = oracle.dslash_oe(L, Ue, effective_vec(xe, prec))
-    with stag.Context(L) as ctx:
+    with stag.Context(L, recon12=recon) as ctx:
         ctx.links_upload(torch.from_numpy(U).cuda())
         xd = torch.from_numpy(xe).cuda()
         g = ctx.mdagm(xd, m, PREC[prec]).cpu().numpy()
