@@ -93,7 +93,11 @@ def l2_note(L, prec, links, l2_persisting):
     """What the L2 holds during the timed solves (the launch form decides)."""
     mb = link_mb(L, prec, links)
     head = "flushed before every timed solve (256 MiB write); "
-    if l2_persisting:
+    if l2_persisting == "vectors":
+        return head + (f"during the solve the Krylov vectors r, x, p, t are an L2 access-policy window whose "
+                       f"lines persist; the links ({mb:.0f} MB) stream; persisting lines are released after "
+                       "every solve")
+    if l2_persisting in (True, "links"):
         return head + (f"during the solve the inner-precision links ({mb:.0f} MB) are an L2 access-policy "
                        "window whose lines persist (set-aside ~85 MB of the 129 MB L2), so most of the two "
                        "link passes per iteration hit L2; the vectors stream; persisting lines are released "
@@ -620,7 +624,7 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else args.precision.replace("fp", "f"),
             "data": "synthetic",
             "config": workload_config(L, masses, args.tol, args.precision, args.links, nrhs,
-                                      form["l2_persisting_links"]),
+                                      form["l2_persisting"]),
             "time_to_solution_ms": ms_step,
             "time_to_solution_ms_best": min(step_ms), "time_to_solution_ms_median": statistics.median(step_ms),
             "iters": iters[-1] if nsys > 1 else iters[-1][0],

@@ -320,7 +320,8 @@ int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps
  * solve (or timing call): out[0] systems per thread, out[1] system groups,
  * out[2] / out[3] lanes per site of the first / second kernel, out[4] link
  * path (0 plane layout, 1 tiled through shared memory, 2 tiled into
- * registers), out[5] 1 when the links persist in L2 during the solve, out[6]
+ * registers), out[5] what persists in L2 during the solve (0 nothing, 1 the
+ * links, 2 the Krylov vectors), out[6]
  * CG iterations per pass of the solve loop, out[7] 1 when the CG kernels
  * share each chunk's links in shared memory among the out[0] systems of a
  * block (one warp per system), 2 when every block runs every system on

@@ -71,11 +71,28 @@ struct DevBuf {
   }
 };
 
-// a set of nsys checkerboard vectors at one storage precision
+// a set of nsys checkerboard vectors at one storage precision: its own
+// allocation (ensure) or a view into a shared pool (set_view)
 struct VecBuf {
   DevBuf data, scale;
+  void *vdata = nullptr;   // view: data and scale inside another buffer (not owned)
+  float *vscale = nullptr;
+  size_t vbytes = 0;
   int prec = -1, nsys = 0, Ve = 0;
+  void set_view(int P, int ns, int ve, void *d, float *sc, size_t bytes) {
+    vdata = d;
+    vscale = sc;
+    vbytes = bytes;
+    prec = P;
+    nsys = ns;
+    Ve = ve;
+  }
+  void *dptr() const { return vdata ? vdata : data.p; }
+  size_t dbytes() const { return vdata ? vbytes : data.n; }
+  float *sptr() const { return vdata ? vscale : (float *)scale.p; }
   cudaError_t ensure(int P, int ns, int ve) {
+    vdata = nullptr;
+    vscale = nullptr;
     cudaError_t e = data.ensure(cplx_bytes(P) * 3ull * ns * ve);
     if (e != cudaSuccess) return e;
     if (P == P16 || P == PBF) {
@@ -89,8 +106,8 @@ struct VecBuf {
   }
   VecArg arg() const {
     VecArg a;
-    a.v = data.p;
-    a.scale = (float *)scale.p;
+    a.v = dptr();
+    a.scale = sptr();
     a.sstr = 3ll * Ve;
     return a;
   }
@@ -126,7 +143,7 @@ struct Work {
   int lanes_k1 = 1, lanes_k2 = 1;  // lanes of the two CG kernels (tuned with their epilogues)
   int nbx_k1 = 0, nbx_k2 = 0;      // blocks per system group of the two CG kernels
   int tma = 0;                     // link path of the CG kernels (DsArgs::tma)
-  int l2p = 0;                     // their links persist in L2 during a solve
+  int l2p = 0;                     // L2 persistence during a solve: 1 the links, 2 the Krylov vectors
   int mrhs = 0;                    // > 0: the CG kernels are k_dslash_mrhs with mrhs systems per block
   int ms = 0;                      // > 0: multi-shift CG, ms shifted systems ride on each system
   int nrhs_sl = 0;                 // > 0: the CG kernels are k_cg_nrhs (every system in every block,
@@ -135,6 +152,7 @@ struct Work {
   const void *links_tile = nullptr;
   int nbx_bl = 0, pstride = 0;
   VecBuf b64, x64, t64, r, x, p, t;
+  DevBuf vpool;  // r, x, p, t (and their scales) in one range: one L2 window can cover them
   DevBuf st, partials, tickets, flags;
   DevBuf st2, partials2;  // second buffers of the states and partials (folded reductions)
   PinnedBuf h_st, h_flags;
@@ -190,7 +208,7 @@ struct stag_ctx {
   // of their traffic streams), so of the two passes over the links per
   // iteration most hit L2; the persisting lines are released after the solve
   bool l2persist = true;  // the device supports it and it is not switched off
-  int l2_modes = 0b11;    // bit p: the tuner may choose persisting links p (STAG_L2PERSIST = 0 or 1 fixes it)
+  int l2_modes = 0b11;    // 0b11: by rule; else bit p: the tuner may choose L2 mode p (STAG_L2PERSIST fixes it)
   size_t l2_max_persist = 0, l2_max_window = 0;
   DevBuf links_canon;  // [4][V][3][3] FP64, kept for lazy reduced-precision copies
   DevBuf links64;
@@ -341,18 +359,24 @@ int links_tile_for(stag_ctx *c, int P, const void **out) {
 // never mark anything persisting) most of their L2 hits.
 void l2_setaside(stag_ctx *c, bool on) {
   if (!c->l2persist) return;
-  cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, on ? c->l2_max_persist : 0);
+  // persisting vectors need only their own size set aside; the rest of L2 stays
+  // with the streaming links
+  size_t want = c->l2_max_persist;
+  if (c->w.l2p == 2 && c->w.vpool.n < want) want = c->w.vpool.n;
+  cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, on ? want : 0);
   cudaGetLastError();
 }
 
-// the L2 window of the CG kernels' links for link path tma (DsArgs::tma)
+// the L2 window of the CG kernels: on = 1 their links (link path tma,
+// DsArgs::tma), on = 2 the Krylov vectors r, x, p, t of the workspace
 void set_l2_window(stag_ctx *c, int P, int tma, int on, DsArgs &a) {
   a.l2_base = nullptr;
   a.l2_bytes = 0;
   a.l2_hit = 0.f;
   if (!c->l2persist || !on) return;
   const int rc = (P != P64 && (c->flags & STAG_RECON12)) ? 1 : 0;
-  const DevBuf &b = (P == P64) ? c->links64 : (tma ? c->links_tile[P][rc] : c->links_lo[P][rc]);
+  const DevBuf &b = (on == 2) ? c->w.vpool
+                              : (P == P64) ? c->links64 : (tma ? c->links_tile[P][rc] : c->links_lo[P][rc]);
   if (!b.p || b.n == 0) return;
   a.l2_base = b.p;
   a.l2_bytes = b.n < c->l2_max_window ? b.n : c->l2_max_window;
@@ -583,7 +607,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
   }
   const bool fl = fl1 != 0;
   std::vector<CgForm> cand;
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < 3; ++p)
     for (int t = 0; t < 3; ++t)
       for (int l1 = 1; l1 <= 2; ++l1)
         for (int l2 = 1; l2 <= 2; ++l2)
@@ -600,7 +624,7 @@ int tune_cg_pair(stag_ctx *c, int LP, int recon, int VP, int NS, int EPI1, DsArg
     return STAG_OK;
   }
   const int G = a1.ngroups;
-  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, (G * 8 + modes) * 4 + l2modes, c->dims[0], c->dims[1],
+  const TuneKey key(LP, recon, VP, NS * 16 + EPI1 + 8, (G * 8 + modes) * 8 + l2modes, c->dims[0], c->dims[1],
                     c->dims[2], c->dims[3]);
   if (!fl && !ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -760,10 +784,18 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
   CK(w.b64.ensure(P64, nsys, Ve));
   CK(w.x64.ensure(P64, nsys, Ve));
   CK(w.t64.ensure(P64, nsys, Ve));
-  CK(w.r.ensure(w.RP, nsys, Ve));
-  CK(w.x.ensure(w.RP, nsys, Ve));
-  CK(w.p.ensure(VP, nsys, Ve));
-  CK(w.t.ensure(VP, nsys, Ve));
+  {
+    // r, x_lo (RP) and p, t (VP) with their scales, 256-byte aligned, in one pool
+    const size_t rb = (cplx_bytes(w.RP) * 3ull * nsys * Ve + 255) & ~(size_t)255;
+    const size_t vb = (cplx_bytes(VP) * 3ull * nsys * Ve + 255) & ~(size_t)255;
+    const size_t sb = (VP == P16 || VP == PBF) ? ((sizeof(float) * (size_t)nsys * Ve + 255) & ~(size_t)255) : 0;
+    CK(w.vpool.ensure(2 * rb + 2 * vb + 2 * sb));
+    char *b = (char *)w.vpool.p;
+    w.r.set_view(w.RP, nsys, Ve, b, nullptr, rb);
+    w.x.set_view(w.RP, nsys, Ve, b + rb, nullptr, rb);
+    w.p.set_view(VP, nsys, Ve, b + 2 * rb, sb ? (float *)(b + 2 * rb + 2 * vb) : nullptr, vb);
+    w.t.set_view(VP, nsys, Ve, b + 2 * rb + vb, sb ? (float *)(b + 2 * rb + 2 * vb + sb) : nullptr, vb);
+  }
   CK(w.st.ensure(sizeof(SysState) * nsys));
   CK(w.partials.ensure(sizeof(double) * (size_t)nsys * NVMAX * w.pstride));
   CK(w.st2.ensure(sizeof(SysState) * nsys));
@@ -777,10 +809,8 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
   CK(cudaMemsetAsync(w.st.p, 0, sizeof(SysState) * nsys, c->stream));
   CK(cudaMemsetAsync(w.st2.p, 0, sizeof(SysState) * nsys, c->stream));
   // defined contents for the timing entry point before any solve
-  CK(cudaMemsetAsync(w.p.data.p, 0, w.p.data.n, c->stream));
-  if (w.p.scale.p) CK(cudaMemsetAsync(w.p.scale.p, 0, w.p.scale.n, c->stream));
+  CK(cudaMemsetAsync(w.vpool.p, 0, w.vpool.n, c->stream));  // r, x, p, t and scales
   CK(cudaMemsetAsync(w.x64.data.p, 0, w.x64.data.n, c->stream));
-  CK(cudaMemsetAsync(w.r.data.p, 0, w.r.data.n, c->stream));
   const void *lo = nullptr;
   CKS(links_for(c, prec, &lo));
   {
@@ -1969,9 +1999,11 @@ int stag_create(const int dims[4], int flags, void *cuda_stream, stag_ctx **out)
     return STAG_ERR_CUDA;
   }
   {
+    // STAG_L2PERSIST = 0 off, 1 the links persist, 2 the Krylov vectors persist
     const char *l2p = getenv("STAG_L2PERSIST");
     c->l2persist = !(l2p && l2p[0] == '0');
-    if (l2p && l2p[0] == '1') c->l2_modes = 0b10;
+    if (l2p && l2p[0] == '1') c->l2_modes = 0b010;
+    if (l2p && l2p[0] == '2') c->l2_modes = 0b100;
     int maxp = 0, maxw = 0;
     if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, c->device) != cudaSuccess)

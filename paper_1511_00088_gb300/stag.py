@@ -519,7 +519,8 @@ class Context:
         st, f = stag_solve_form(self.h)
         self._check(st)
         return {"systems_per_thread": f[0], "groups": f[1], "lanes_k1": f[2], "lanes_k2": f[3],
-                "link_path": ("planes", "tiled_smem", "tiled")[f[4]], "l2_persisting_links": bool(f[5]),
+                "link_path": ("planes", "tiled_smem", "tiled")[f[4]], "l2_persisting_links": f[5] == 1,
+                "l2_persisting": ("none", "links", "vectors")[f[5]],
                 "iterations_per_pass": f[6], "shared_memory_links": bool(f[7]),
                 "kernels": ("k_dslash", "k_dslash_mrhs", "k_cg_nrhs")[f[7]]}
 
