@@ -44,6 +44,11 @@ FLOP_PER_SITE_ITER = 1212     # 2 x 570 (two half operators) + 12 (mass) + 5 x 1
 DSLASH_FLOP_PER_SITE = 570    # 8 x 66 (SU(3) x vector) + 7 x 6 (accumulation)
 PAPER_TX_CG_GFLOPS = 107.7    # Titan X, mixed CG, 20^3 x 64, one GPU (Table 2 of the paper)
 L2_FLUSH_BYTES = 256 << 20
+# NPR contraction per hypercube, as the kernel computes it: 512 products of 3x3
+# complex matrices for the 256 shortest-path averages (198 flop each) plus their
+# sums and scalings (~4k), and 256 terms of two colour contractions (2 x 88 flop)
+# and their product (6): 512*198 + 4096 + 256*182
+NPR_FLOP_PER_HYPERCUBE = 512 * 198 + 4096 + 256 * 182
 
 
 def parse():
@@ -348,6 +353,20 @@ def batched_extras(stream, hbm):
         e1.synchronize()
         out["hyp_smear_20x64_fp64"] = {"ms": e0.elapsed_time(e1), "links": 4 * V}
         del H
+        # the NPR one-colour-trace four-fermion contraction (Sec. 4, FP64) on the
+        # same field: four Gaussian colour-vector fields, spin-taste (S1,F1,S2,F2)
+        # = (15, 0, 15, 0); flops by the kernel's arithmetic per hypercube
+        fs = [torch.from_numpy(synth.gaussian_vector(V, synth.seed_for(2, 400 + k))).cuda() for k in range(4)]
+        ctx.npr_contract((15, 0, 15, 0), *fs)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.npr_contract((15, 0, 15, 0), *fs)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["npr_contraction_20x64_fp64"] = {"ms": ms, "hypercubes": V // 16,
+                                             "GFLOP/s": NPR_FLOP_PER_HYPERCUBE * (V // 16) / (ms * 1e-3) / 1e9,
+                                             "flop_per_hypercube": NPR_FLOP_PER_HYPERCUBE}
     out["config2_12src_x_4mass_20x64"] = c2
     del U, bs
     # the ragged batch: one source x the 4 masses on each of four lattices, one graph
