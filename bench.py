@@ -44,11 +44,13 @@ FLOP_PER_SITE_ITER = 1212     # 2 x 570 (two half operators) + 12 (mass) + 5 x 1
 DSLASH_FLOP_PER_SITE = 570    # 8 x 66 (SU(3) x vector) + 7 x 6 (accumulation)
 PAPER_TX_CG_GFLOPS = 107.7    # Titan X, mixed CG, 20^3 x 64, one GPU (Table 2 of the paper)
 L2_FLUSH_BYTES = 256 << 20
-# NPR contraction per hypercube, as the kernel computes it: 512 products of 3x3
-# complex matrices for the 256 shortest-path averages (198 flop each) plus their
-# sums and scalings (~4k), and 256 terms of two colour contractions (2 x 88 flop)
-# and their product (6): 512*198 + 4096 + 256*182
-NPR_FLOP_PER_HYPERCUBE = 512 * 198 + 4096 + 256 * 182
+# NPR contraction per hypercube, as the kernel computes it: the 120 path
+# averages W(A, D), A < D (the rest are adjoints or 1), at |A xor D| = n from n
+# products with a step link -- 32 copies at n = 1, 48 x 2 + 32 x 3 + 8 x 4 = 224
+# products of 3x3 complex matrices (27 complex multiply-adds = 216 flop each)
+# for n >= 2 -- and 256 terms of two colour contractions (2 x 12 complex
+# multiply-adds) and their product: 224*216 + 256*(24*8 + 6)
+NPR_FLOP_PER_HYPERCUBE = 224 * 216 + 256 * (24 * 8 + 6)
 
 
 def parse():

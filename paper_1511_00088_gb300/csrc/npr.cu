@@ -9,8 +9,9 @@
 //   hypercube of the link products (U_mu for +mu, U_mu^dag for -mu).
 // One block per hypercube, 256 threads:
 //   * its 32 internal links into shared memory;
-//   * the 256 path averages W(A, D), level by level in |A xor D|: a path's
-//     last step is one of the differing directions mu, so
+//   * the path averages W(A, D) for A < D (W(D, A) = W(A, D)^dag, W(A, A) =
+//     1), level by level in n = |A xor D|, one thread per matrix element: a
+//     path's last step is one of the differing directions mu, so
 //     W(A, D) = (1/n) sum_mu W(A, D xor mu) step(D xor mu -> D);
 //   * the spin-taste entries from the Clifford algebra: g_X g_Y = e(X, Y)
 //     g_{X xor Y} with e(X, Y) = (-1)^(sum_{mu > nu} X_mu Y_nu), g_A^dag =
@@ -97,57 +98,63 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
     const double2 *src = f == 0 ? a.cb1 : f == 1 ? a.c2 : f == 2 ? a.cb3 : a.c4;
     fld[f][A][c] = src[site(A) * 3 + c];
   }
-  const int A = t >> 4, D = t & 15;
-  if (A == D) {
-#pragma unroll
-    for (int e = 0; e < 9; ++e) W[t][e] = make_double2((e % 4 == 0) ? 1.0 : 0.0, 0.0);
+  // W(A, A) = 1; the pairs A < D level by level in n = |A xor D|, one thread
+  // per (pair, element); W(D, A) = W(A, D)^dag is read from the A < D entry
+  for (int k = t; k < 16 * 9; k += NPR_BT) {
+    const int Y = k / 9, e = k % 9;
+    W[Y * 17][e] = make_double2((e % 4 == 0) ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
-  // path averages, level by level
   for (int n = 1; n <= 4; ++n) {
-    if (__popc(A ^ D) == n) {
-      double2 acc[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) acc[e] = make_double2(0.0, 0.0);
+    for (int item = t; item < 256 * 9; item += NPR_BT) {
+      const int pr = item / 9, e = item % 9;
+      const int A = pr >> 4, D = pr & 15;
+      if (!(A < D && __popc(A ^ D) == n)) continue;
+      const int i = e / 3, j = e % 3;
+      if (n == 1) {  // one step: the link itself (forward) or its adjoint
+        const int mu = __ffs(A ^ D) - 1;
+        const bool fwd = (D >> mu) & 1;
+        const double2 *u = fwd ? lk[lslot(A, mu)] : lk[lslot(D, mu)];
+        W[A * 16 + D][e] = fwd ? u[i * 3 + j] : make_double2(u[j * 3 + i].x, -u[j * 3 + i].y);
+        continue;
+      }
+      double2 s = make_double2(0.0, 0.0);
       for (int mu = 0; mu < 4; ++mu) {
         if (!(((A ^ D) >> mu) & 1)) continue;
         const int P = D ^ (1 << mu);  // the corner before the last step
         const bool fwd = (D >> mu) & 1;  // +mu from P to D: U_mu(z_P); else -mu: U_mu(z_D)^dag
-        const double2 *Wp = W[A * 16 + P];
         const double2 *u = fwd ? lk[lslot(P, mu)] : lk[lslot(D, mu)];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const double2 st = fwd ? u[k * 3 + j] : make_double2(u[j * 3 + k].x, -u[j * 3 + k].y);
-              s = za(s, zm(Wp[i * 3 + k], st));
-            }
-            acc[i * 3 + j] = za(acc[i * 3 + j], s);
-          }
+        for (int k = 0; k < 3; ++k) {
+          // W(A, P)[i][k], from the stored A <= P or P < A entry
+          const double2 w = (A <= P) ? W[A * 16 + P][i * 3 + k]
+                                     : make_double2(W[P * 16 + A][k * 3 + i].x, -W[P * 16 + A][k * 3 + i].y);
+          const double2 st = fwd ? u[k * 3 + j] : make_double2(u[j * 3 + k].x, -u[j * 3 + k].y);
+          s = za(s, zm(w, st));
+        }
       }
       const double inv = 1.0 / n;
-#pragma unroll
-      for (int e = 0; e < 9; ++e) W[t][e] = make_double2(acc[e].x * inv, acc[e].y * inv);
+      W[A * 16 + D][e] = make_double2(s.x * inv, s.y * inv);
     }
     __syncthreads();
   }
   // thread (A, C): its term
-  const int C = D;
+  const int A = t >> 4, C = t & 15;
   const int B = A ^ a.S1 ^ a.F1, Dd = C ^ a.S2 ^ a.F2;
   const double s = spin_taste(a.S1, a.F1, A, B) * spin_taste(a.S2, a.F2, C, Dd);
   double2 t1 = make_double2(0.0, 0.0), t2 = make_double2(0.0, 0.0);
   {
-    const double2 *wad = W[A * 16 + Dd], *wcb = W[C * 16 + B];
+    // element (i, j) of W(X, Y) from the stored X <= Y entry (adjoint otherwise)
+    auto wget = [&](int X, int Y, int i, int j) -> double2 {
+      return X <= Y ? W[X * 16 + Y][i * 3 + j] : make_double2(W[Y * 16 + X][j * 3 + i].x, -W[Y * 16 + X][j * 3 + i].y);
+    };
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       double2 v1 = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        v1 = za(v1, zm(wad[i * 3 + j], fld[3][Dd][j]));
-        v2 = za(v2, zm(wcb[i * 3 + j], fld[1][B][j]));
+        v1 = za(v1, zm(wget(A, Dd, i, j), fld[3][Dd][j]));
+        v2 = za(v2, zm(wget(C, B, i, j), fld[1][B][j]));
       }
       t1 = za(t1, zm(fld[0][A][i], v1));
       t2 = za(t2, zm(fld[2][C][i], v2));
