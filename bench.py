@@ -76,6 +76,9 @@ def parse():
                     help="profiling runs: skip the comparison solves, the e2e leg and the CPU baseline")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched / 48^3x96 extras (config 2, ragged, config 4, HBM-bound kernels)")
+    ap.add_argument("--probe", default=None, choices=["npr", "hyp"],
+                    help="time only the NPR contraction or the HYP smearing on --lattice (profiling runs); "
+                         "prints one JSON line")
     return ap.parse_args()
 
 
@@ -667,10 +670,55 @@ def run_ours(args):
     return 0
 
 
+def run_probe(args):
+    """--probe: time one FP64 side workload of the paper on --lattice: the NPR
+    contraction (Sec. 4; spin-taste (15, 0, 15, 0), four Gaussian fields) or
+    the HYP smearing of the field (Sec. 3's smeared links)."""
+    import torch
+
+    from paper_1511_00088_gb300 import build as B
+    from paper_1511_00088_gb300 import stag, synth
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    B.build()
+    stag.load()
+    L = tuple(int(v) for v in args.lattice.split(","))
+    V = synth.volume(L)
+    U = (synth.random_links_device(L, 0.4, synth.seed_for(2, 1), device="cuda") if V > (1 << 22)
+         else torch.from_numpy(synth.random_links(L, 0.4, synth.seed_for(2, 1))).cuda())
+    stream = torch.cuda.current_stream()
+    with stag.Context(L, stream=stream.cuda_stream) as ctx:
+        ctx.links_upload(U)
+        if args.probe == "npr":
+            fs = [torch.from_numpy(synth.gaussian_vector(V, synth.seed_for(2, 400 + k))).cuda() for k in range(4)]
+            op = lambda: ctx.npr_contract((15, 0, 15, 0), *fs)  # noqa: E731
+        else:
+            H = torch.empty_like(U)
+            op = lambda: ctx.hyp_smear(U, out=H)  # noqa: E731
+        for _ in range(args.warmup):
+            op()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            op()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    line = {"probe": args.probe, "lattice": list(L), "ms": ms, "steps": args.steps, "warmup": args.warmup}
+    if args.probe == "npr":
+        line["GFLOP/s"] = NPR_FLOP_PER_HYPERCUBE * (V // 16) / (ms * 1e-3) / 1e9
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.probe:
+        return run_probe(args)
     return run_ours(args)
 
 
