@@ -34,6 +34,10 @@ __device__ __forceinline__ double2 cm(double2 x, double2 y) { return make_double
 __device__ __forceinline__ double2 cadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
 __device__ __forceinline__ double2 csub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
 __device__ __forceinline__ double2 ccj(double2 x) { return make_double2(x.x, -x.y); }
+// s + x y as two FMA chains per component (4 FP64 instructions for 8 flops)
+__device__ __forceinline__ double2 cfma(double2 x, double2 y, double2 s) {
+  return make_double2(__fma_rn(-x.y, y.y, __fma_rn(x.x, y.x, s.x)), __fma_rn(x.y, y.x, __fma_rn(x.x, y.y, s.y)));
+}
 
 __device__ __forceinline__ M3 ld(const double2 *p) {
   M3 m;
@@ -55,7 +59,7 @@ __device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
       for (int k = 0; k < 3; ++k) {
         const double2 x = DA ? ccj(a.a[k * 3 + i]) : a.a[i * 3 + k];
         const double2 y = DB ? ccj(b.a[j * 3 + k]) : b.a[k * 3 + j];
-        s = cadd(s, cm(x, y));
+        s = cfma(x, y, s);
       }
       c.a[i * 3 + j] = s;
     }

@@ -417,7 +417,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int ma
   return false;
 }
 
-// acc += sgn * (U v)
+// a * b + c, one rounding (FMA) at either precision
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// acc += sgn * (U v).  In FP64 every complex multiply-accumulate is two FMA
+// chains per component (re += ur vr - ui vi, im += ur vi + ui vr): 4
+// instructions for 8 flops where a*b - c*d + h takes 6, which matters because
+// the FP64 operator is bound by GB300's FP64 pipe (~87 % busy).  FP32 keeps
+// the expression form: the chains cost the memory-bound FP32 kernels
+// registers (123 -> 138 for the second CG kernel, one block fewer per SM).
 template <class R>
 __device__ __forceinline__ void mv_acc(const R (&u)[18], const R (&v)[6], R sgn, R (&acc)[6]) {
 #pragma unroll
@@ -426,8 +435,15 @@ __device__ __forceinline__ void mv_acc(const R (&u)[18], const R (&v)[6], R sgn,
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const R ur = u[2 * (3 * a + b)], ui = u[2 * (3 * a + b) + 1];
-      hr += ur * v[2 * b] - ui * v[2 * b + 1];
-      hi += ur * v[2 * b + 1] + ui * v[2 * b];
+      if (sizeof(R) == 8) {
+        hr = fmar(ur, v[2 * b], hr);
+        hr = fmar(-ui, v[2 * b + 1], hr);
+        hi = fmar(ur, v[2 * b + 1], hi);
+        hi = fmar(ui, v[2 * b], hi);
+      } else {
+        hr += ur * v[2 * b] - ui * v[2 * b + 1];
+        hi += ur * v[2 * b + 1] + ui * v[2 * b];
+      }
     }
     acc[2 * a] += sgn * hr;
     acc[2 * a + 1] += sgn * hi;
@@ -443,8 +459,15 @@ __device__ __forceinline__ void mvdag_acc(const R (&u)[18], const R (&v)[6], R s
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const R ur = u[2 * (3 * b + a)], ui = u[2 * (3 * b + a) + 1];
-      hr += ur * v[2 * b] + ui * v[2 * b + 1];
-      hi += ur * v[2 * b + 1] - ui * v[2 * b];
+      if (sizeof(R) == 8) {
+        hr = fmar(ur, v[2 * b], hr);
+        hr = fmar(ui, v[2 * b + 1], hr);
+        hi = fmar(ur, v[2 * b + 1], hi);
+        hi = fmar(-ui, v[2 * b], hi);
+      } else {
+        hr += ur * v[2 * b] + ui * v[2 * b + 1];
+        hi += ur * v[2 * b + 1] - ui * v[2 * b];
+      }
     }
     acc[2 * a] += sgn * hr;
     acc[2 * a + 1] += sgn * hi;
