@@ -74,13 +74,17 @@ __device__ __forceinline__ double2 det3(const M3 &m) {
   return cadd(cadd(cm(a[0], t0), cm(a[1], t1)), cm(a[2], t2));
 }
 
-// P(X): scaled Newton polar iteration, then the determinant's phase removed
+// P(X): scaled Newton polar iteration, then the determinant's phase removed.
+// Scaling while a step still changes Y by more than 1 % (relative); the
+// iteration stops after a step that changed it by less than 1e-12, which by
+// the quadratic convergence leaves Y within ~1e-24 of the polar factor.
 __device__ M3 project_su3(const M3 &X) {
   M3 Y = X;
+  bool scaled = true;
   for (int it = 0; it < 60; ++it) {
     const double2 d = det3(Y);
     const double ad = sqrt(d.x * d.x + d.y * d.y);
-    const double g = (it < 6) ? cbrt(1.0 / ad) : 1.0;  // scaling only while far from unitary
+    const double g = scaled ? cbrt(1.0 / ad) : 1.0;
     // (g Y)^-dag = (1/g) adj(Y)^dag / conj(det Y): entry (i, j) = conj(cof_ij(Y)) / (g conj(det))
     const double inv = 1.0 / (g * (d.x * d.x + d.y * d.y));
     M3 N;
@@ -101,7 +105,8 @@ __device__ M3 project_su3(const M3 &X) {
         N.a[i * 3 + j] = n;
       }
     Y = N;
-    if (it >= 6 && diff <= 1e-32 * nrm) break;
+    if (!scaled && diff <= 1e-24 * nrm) break;
+    if (diff <= 1e-4 * nrm) scaled = false;
   }
   const double2 d = det3(Y);
   const double ph = atan2(d.y, d.x) / 3.0;
