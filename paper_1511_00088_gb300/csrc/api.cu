@@ -536,7 +536,7 @@ int nrhs_blocks(stag_ctx *c, int recon, int sl, int EPI, int *nb) {
   const void *k = nullptr;
   CK(launch_cg_nrhs(recon, sl, EPI, 0, c->stream, none, &k));
   int per_sm = 0, nsm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * (sl % 10), cg_nrhs_smem(recon, sl)));  // sl % 10: threads per site
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * (sl % 10), cg_nrhs_smem(recon, sl)));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   int n = per_sm * nsm;
   if (n < 1) n = 1;
@@ -871,11 +871,11 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
     // STAG_NRHS = 2 or 4: this form with that many threads per site (two link
     // stages), 14: 4 threads per site with one stage (3 blocks per SM; measured
     // slower: 48-system 20^3 x 64 solve 3.34 s vs 2.36 s, so not a default
-    // candidate), 24: 4 threads per site, two systems per pass; 0: never this form
+    // candidate); 0: never this form
     const char *fnr = getenv("STAG_NRHS");
     if (fnr && nrhs_ok) {
       const int f = atoi(fnr);
-      if (f == 2 || f == 4 || f == 14 || f == 24) cands.assign(1, 200 + f);
+      if (f == 2 || f == 4 || f == 14) cands.assign(1, 200 + f);
     }
     if (fnr && fnr[0] == '0' && fnr[1] == 0) {
       std::vector<int> keep;
@@ -937,7 +937,7 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
       // are one grid of nbx_k1 / nbx_k2 blocks, each a partial per system
       CKS(links_tile_for(c, prec, &w.links_tile));
       w.tma = 1;
-      w.lanes_k1 = w.lanes_k2 = w.nrhs_sl % 10;  // threads per site of the form
+      w.lanes_k1 = w.lanes_k2 = w.nrhs_sl % 10;
       w.l2p = 0;
       CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K1R, &w.nbx_k1));
       CKS(nrhs_blocks(c, recon, w.nrhs_sl, EPI_CG_K2, &w.nbx_k2));

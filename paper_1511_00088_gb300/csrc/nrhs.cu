@@ -70,62 +70,6 @@ __device__ __forceinline__ void mvdag_x2(const float2 *u, int ls, const float2 (
   }
 }
 
-// the same for JJ systems at once: each link element, read once from shared
-// memory, is applied to all of them
-template <int JJ>
-__device__ __forceinline__ void mv_x2n(const float2 *u, int ls, const float2 (&v)[JJ][3], float sgn,
-                                       float2 (&acc)[JJ][3]) {
-  float2 w[JJ][3];
-#pragma unroll
-  for (int q = 0; q < JJ; ++q)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) w[q][b] = make_float2(-v[q][b].y, v[q][b].x);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float2 h[JJ];
-#pragma unroll
-    for (int q = 0; q < JJ; ++q) h[q] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2 e = u[(3 * a + b) * ls];
-#pragma unroll
-      for (int q = 0; q < JJ; ++q) {
-        h[q] = __ffma2_rn(bc2(e.x), v[q][b], h[q]);
-        h[q] = __ffma2_rn(bc2(e.y), w[q][b], h[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < JJ; ++q) acc[q][a] = __ffma2_rn(bc2(sgn), h[q], acc[q][a]);
-  }
-}
-
-template <int JJ>
-__device__ __forceinline__ void mvdag_x2n(const float2 *u, int ls, const float2 (&v)[JJ][3], float sgn,
-                                          float2 (&acc)[JJ][3]) {
-  float2 w[JJ][3];
-#pragma unroll
-  for (int q = 0; q < JJ; ++q)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) w[q][b] = make_float2(v[q][b].y, -v[q][b].x);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float2 h[JJ];
-#pragma unroll
-    for (int q = 0; q < JJ; ++q) h[q] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2 e = u[(3 * b + a) * ls];
-#pragma unroll
-      for (int q = 0; q < JJ; ++q) {
-        h[q] = __ffma2_rn(bc2(e.x), v[q][b], h[q]);
-        h[q] = __ffma2_rn(bc2(e.y), w[q][b], h[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < JJ; ++q) acc[q][a] = __ffma2_rn(bc2(sgn), h[q], acc[q][a]);
-  }
-}
-
 // the three colours of site s of system k (FP32 vector, read-only path)
 __device__ __forceinline__ void ld3(const VecArg &f, int k, int s, int Ve, float2 (&v)[3]) {
   const float2 *p = reinterpret_cast<const float2 *>(f.v) + (long long)k * f.sstr + s;
@@ -159,11 +103,8 @@ inline unsigned nrhs_smem_bytes(int recon, int stg) {
 // STG = 2: two stages, the next tile's copy in flight during the whole round
 // (2 blocks per SM); STG = 1: one stage, refilled as soon as this round's
 // links are in the full copy (less shared memory: 3 blocks per SM)
-// JJ = 1 or 2: systems a thread takes per pass (JJ = 2: both systems'
-// neighbours in flight together, each link element from shared memory applied
-// to both; more registers, one block per SM)
-template <int RECON, int EPI, int SL, int STG, int JJ>
-__global__ void __launch_bounds__(LT * SL, JJ == 2 ? 1 : (STG == 1 ? 3 : 2)) k_cg_nrhs(const DsArgs a) {
+template <int RECON, int EPI, int SL, int STG>
+__global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsArgs a) {
   static_assert(EPI == EPI_CG_K1R || EPI == EPI_CG_K2, "the two CG kernels");
   static_assert(STG == 1 || STG == 2, "one or two stages");
   constexpr int BT = LT * SL;
@@ -291,89 +232,60 @@ __global__ void __launch_bounds__(LT * SL, JJ == 2 ? 1 : (STG == 1 ? 3 : 2)) k_c
         }
       }
     }
-    for (int j0 = lane * JJ; j0 < nsys; j0 += SL * JJ) {
-      bool on[JJ];
-      float beta[JJ], alpha[JJ], m4[JJ], q0[JJ], q1[JJ];
-#pragma unroll
-      for (int q = 0; q < JJ; ++q) {
-        const int j = j0 + q;
-        on[q] = j < nsys && sf32[j < nsys ? j : 0].act;  // uniform per warp
-        const SysF S = sf32[j < nsys ? j : 0];
-        beta[q] = S.beta;
-        alpha[q] = S.alpha;
-        m4[q] = S.m4;
-        q0[q] = q1[q] = 0.f;
-      }
-      bool any = false;
-#pragma unroll
-      for (int q = 0; q < JJ; ++q) any |= on[q];
-      if (!any) continue;
+    for (int j = lane; j < nsys; j += SL) {
+      const SysF S = sf32[j];
+      if (!S.act) continue;  // uniform per warp
+      const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
+      float q0 = 0.f, q1 = 0.f;
       if (valid) {
-        float2 vf[4][JJ][3], vb[4][JJ][3], c0[JJ][3], c1[JJ][3], c2[JJ][3];
-#pragma unroll
-        for (int q = 0; q < JJ; ++q) {
-          const int j = on[q] ? j0 + q : j0;  // an inactive second system re-reads the first's (never stored)
-#pragma unroll
-          for (int mu = 0; mu < 4; ++mu) {
-            ld3(a.in, j, sf[mu], Ve, vf[mu][q]);
-            ld3(a.in, j, sb[mu], Ve, vb[mu][q]);
-          }
-          if (EPI == EPI_CG_K2) {
-            ld3_rw(a.center, j, s, Ve, c0[q]);
-            ld3_rw(a.aux, j, s, Ve, c1[q]);
-            ld3_rw(a.xlo, j, s, Ve, c2[q]);
-          } else {
-            ld3_rw(a.out, j, s, Ve, c0[q]);
-          }
-        }
-        float2 acc[JJ][3];
-#pragma unroll
-        for (int q = 0; q < JJ; ++q)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) acc[q][k] = make_float2(0.f, 0.f);
+        float2 vf[4][3], vb[4][3], c0[3], c1[3], c2[3];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-          mv_x2n<JJ>(L + mu * (LNE * LT) + i, LT, vf[mu], bf[mu], acc);
-          mvdag_x2n<JJ>(L + (4 + mu) * (LNE * LT) + i, LT, vb[mu], -bb[mu], acc);
+          ld3(a.in, j, sf[mu], Ve, vf[mu]);
+          ld3(a.in, j, sb[mu], Ve, vb[mu]);
         }
+        if (EPI == EPI_CG_K2) {
+          ld3_rw(a.center, j, s, Ve, c0);
+          ld3_rw(a.aux, j, s, Ve, c1);
+          ld3_rw(a.xlo, j, s, Ve, c2);
+        } else {
+          ld3_rw(a.out, j, s, Ve, c0);
+        }
+        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int q = 0; q < JJ; ++q) {
-          if (!on[q]) continue;
-          const int j = j0 + q;
-          if (EPI == EPI_CG_K2) {
-            // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
+        for (int mu = 0; mu < 4; ++mu) {
+          mv_x2(L + mu * (LNE * LT) + i, LT, vf[mu], bf[mu], acc);
+          mvdag_x2(L + (4 + mu) * (LNE * LT) + i, LT, vb[mu], -bb[mu], acc);
+        }
+        if (EPI == EPI_CG_K2) {
+          // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              c0[q][k] = __ffma2_rn(bc2(beta[q]), c0[q][k], c1[q][k]);
-              const float2 ap = __ffma2_rn(bc2(m4[q]), c0[q][k], make_float2(-acc[q][k].x, -acc[q][k].y));
-              c1[q][k] = __ffma2_rn(bc2(-alpha[q]), ap, c1[q][k]);
-              c2[q][k] = __ffma2_rn(bc2(alpha[q]), c0[q][k], c2[q][k]);
-              q0[q] += c1[q][k].x * c1[q][k].x + c1[q][k].y * c1[q][k].y;
-              q1[q] += c1[q][k].x * c0[q][k].x + c1[q][k].y * c0[q][k].y;
-            }
-            st3(a.center, j, s, Ve, c0[q]);
-            st3(a.aux, j, s, Ve, c1[q]);
-            st3(a.xlo, j, s, Ve, c2[q]);
-          } else {
-            // t = D_oe r + beta t_old
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              c0[q][k] = __ffma2_rn(bc2(beta[q]), c0[q][k], acc[q][k]);
-              q0[q] += c0[q][k].x * c0[q][k].x + c0[q][k].y * c0[q][k].y;
-            }
-            st3(a.out, j, s, Ve, c0[q]);
+          for (int k = 0; k < 3; ++k) {
+            c0[k] = __ffma2_rn(bc2(beta), c0[k], c1[k]);
+            const float2 ap = __ffma2_rn(bc2(m4), c0[k], make_float2(-acc[k].x, -acc[k].y));
+            c1[k] = __ffma2_rn(bc2(-alpha), ap, c1[k]);
+            c2[k] = __ffma2_rn(bc2(alpha), c0[k], c2[k]);
+            q0 += c1[k].x * c1[k].x + c1[k].y * c1[k].y;
+            q1 += c1[k].x * c0[k].x + c1[k].y * c0[k].y;
           }
+          st3(a.center, j, s, Ve, c0);
+          st3(a.aux, j, s, Ve, c1);
+          st3(a.xlo, j, s, Ve, c2);
+        } else {
+          // t = D_oe r + beta t_old
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            c0[k] = __ffma2_rn(bc2(beta), c0[k], acc[k]);
+            q0 += c0[k].x * c0[k].x + c0[k].y * c0[k].y;
+          }
+          st3(a.out, j, s, Ve, c0);
         }
       }
-#pragma unroll
-      for (int q = 0; q < JJ; ++q) {
-        if (!on[q]) continue;
-        const float r0 = warp_sum(q0[q]);
-        const float r1 = (NV > 1) ? warp_sum(q1[q]) : 0.f;
-        if ((tid & 31) == 0) {
-          red[j0 + q][warp][0] += r0;
-          if (NV > 1) red[j0 + q][warp][NV - 1] += r1;
-        }
+      q0 = warp_sum(q0);
+      if (NV > 1) q1 = warp_sum(q1);
+      if ((tid & 31) == 0) {
+        red[j][warp][0] += q0;
+        if (NV > 1) red[j][warp][NV - 1] += q1;
       }
     }
   }
@@ -387,7 +299,7 @@ __global__ void __launch_bounds__(LT * SL, JJ == 2 ? 1 : (STG == 1 ? 3 : 2)) k_c
   // one FP64 partial per system and value: the warps of the system's lane in order
   if (a.ctl.st != nullptr) {
     for (int k = tid; k < nsys * NV; k += BT) {
-      const int j = k / NV, v = k % NV, ln = (j / JJ) % SL;  // the lane that ran system j
+      const int j = k / NV, v = k % NV, ln = j % SL;
       float sum = 0.f;
 #pragma unroll
       for (int w = 0; w < LT / 32; ++w) sum += red[j][ln * (LT / 32) + w][v];
@@ -396,9 +308,9 @@ __global__ void __launch_bounds__(LT * SL, JJ == 2 ? 1 : (STG == 1 ? 3 : 2)) k_c
   }
 }
 
-template <int RC_, int EPI_, int SL_, int STG_, int JJ_>
+template <int RC_, int EPI_, int SL_, int STG_>
 static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **kptr) {
-  auto k = k_cg_nrhs<RC_, EPI_, SL_, STG_, JJ_>;
+  auto k = k_cg_nrhs<RC_, EPI_, SL_, STG_>;
   const unsigned smem = nrhs_smem_bytes(RC_, STG_);
   static bool attr_set = false;  // benign race: setting it twice is harmless
   if (!attr_set) {
@@ -415,19 +327,16 @@ static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const
 
 cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr) {
-#define STAG_NR(RC_, EPI_, SL_, STG_, JJ_)                                     \
-  if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + 20 * (JJ_ - 1) + SL_) \
-    return nrhs_one<RC_, EPI_, SL_, STG_, JJ_>(nblocks, st, a, kptr);
-  STAG_NR(0, EPI_CG_K1R, 2, 2, 1) STAG_NR(0, EPI_CG_K2, 2, 2, 1) STAG_NR(1, EPI_CG_K1R, 2, 2, 1)
-  STAG_NR(1, EPI_CG_K2, 2, 2, 1) STAG_NR(0, EPI_CG_K1R, 4, 2, 1) STAG_NR(0, EPI_CG_K2, 4, 2, 1)
-  STAG_NR(1, EPI_CG_K1R, 4, 2, 1) STAG_NR(1, EPI_CG_K2, 4, 2, 1) STAG_NR(1, EPI_CG_K1R, 4, 1, 1)
-  STAG_NR(1, EPI_CG_K2, 4, 1, 1) STAG_NR(0, EPI_CG_K1R, 4, 1, 1) STAG_NR(0, EPI_CG_K2, 4, 1, 1)
-  STAG_NR(1, EPI_CG_K1R, 4, 2, 2) STAG_NR(1, EPI_CG_K2, 4, 2, 2) STAG_NR(0, EPI_CG_K1R, 4, 2, 2)
-  STAG_NR(0, EPI_CG_K2, 4, 2, 2)
+#define STAG_NR(RC_, EPI_, SL_, STG_)                   \
+  if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + SL_) \
+    return nrhs_one<RC_, EPI_, SL_, STG_>(nblocks, st, a, kptr);
+  STAG_NR(0, EPI_CG_K1R, 2, 2) STAG_NR(0, EPI_CG_K2, 2, 2) STAG_NR(1, EPI_CG_K1R, 2, 2) STAG_NR(1, EPI_CG_K2, 2, 2)
+  STAG_NR(0, EPI_CG_K1R, 4, 2) STAG_NR(0, EPI_CG_K2, 4, 2) STAG_NR(1, EPI_CG_K1R, 4, 2) STAG_NR(1, EPI_CG_K2, 4, 2)
+  STAG_NR(1, EPI_CG_K1R, 4, 1) STAG_NR(1, EPI_CG_K2, 4, 1) STAG_NR(0, EPI_CG_K1R, 4, 1) STAG_NR(0, EPI_CG_K2, 4, 1)
 #undef STAG_NR
   return cudaErrorNotSupported;
 }
 
-unsigned cg_nrhs_smem(int recon, int form) { return nrhs_smem_bytes(recon, (form % 20) >= 10 ? 1 : 2); }
+unsigned cg_nrhs_smem(int recon, int form) { return nrhs_smem_bytes(recon, form >= 10 ? 1 : 2); }
 
 }  // namespace stag

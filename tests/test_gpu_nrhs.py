@@ -4,8 +4,7 @@ oracle and the one-system-per-block form.
 
 Lattices with a ragged last tile (Ve not a multiple of 64), 2..48 systems
 (sources x masses), full and reconstruct-12 links, 2 and 4 threads per site
-with two link stages, 4 with one stage, and 4 with two systems per pass
-(STAG_NRHS = 2, 4, 14, 24):
+with two link stages and 4 with one stage (STAG_NRHS = 2, 4, 14):
 every system's true residual recomputed by the oracle is <= 1e-10.
 """
 import os
@@ -46,7 +45,7 @@ def solve_forced(L, U, bs, masses, recon, nrhs):
 
 @pytest.mark.parametrize("L", [(4, 2, 6, 8), (6, 6, 6, 12), (2, 2, 2, 2), (8, 8, 8, 16)])
 @pytest.mark.parametrize("recon", [False, True])
-@pytest.mark.parametrize("sl", [2, 4, 14, 24])
+@pytest.mark.parametrize("sl", [2, 4, 14])
 def test_nrhs_form_matches_oracle(L, recon, sl):
     V = synth.volume(L)
     U = synth.random_links(L, 0.4, 701)
