@@ -15,7 +15,8 @@
 // removed by the principal cube root.  Here the polar factor comes from
 // Newton's iteration with determinant scaling (Y <- (g Y + (g Y)^-dag) / 2,
 // g = |det Y|^(-1/3); Higham, "Computing the polar decomposition", 1986),
-// which reaches the same unique factor in fewer steps than the plain one.
+// which reaches the same unique factor in fewer steps than the plain one, and
+// the determinant's phase from Newton's iteration for a complex cube root.
 // One thread per (decorated link, site); links in the ABI layout
 // [direction][site][3][3] complex (decorated: [12 (mu, decoration) slots][site][3][3]).
 #include <cuda_runtime.h>
@@ -31,12 +32,16 @@ struct M3 {
 };
 
 __device__ __forceinline__ double2 cm(double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); }
-__device__ __forceinline__ double2 cadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
-__device__ __forceinline__ double2 csub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
 __device__ __forceinline__ double2 ccj(double2 x) { return make_double2(x.x, -x.y); }
 // s + x y as two FMA chains per component (4 FP64 instructions for 8 flops)
 __device__ __forceinline__ double2 cfma(double2 x, double2 y, double2 s) {
   return make_double2(__fma_rn(-x.y, y.y, __fma_rn(x.x, y.x, s.x)), __fma_rn(x.y, y.x, __fma_rn(x.x, y.y, s.y)));
+}
+
+// a b - c e as FMA chains (4 FP64 instructions per component)
+__device__ __forceinline__ double2 cdet2(double2 a, double2 b, double2 c, double2 e) {
+  return make_double2(__fma_rn(a.x, b.x, __fma_rn(-a.y, b.y, __fma_rn(-c.x, e.x, c.y * e.y))),
+                      __fma_rn(a.x, b.y, __fma_rn(a.y, b.x, __fma_rn(-c.x, e.y, (-c.y) * e.x))));
 }
 
 __device__ __forceinline__ M3 ld(const double2 *p) {
@@ -46,15 +51,14 @@ __device__ __forceinline__ M3 ld(const double2 *p) {
   return m;
 }
 
-// c = a b, with either factor optionally daggered
+// c += a b, with either factor optionally daggered
 template <bool DA, bool DB>
-__device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
-  M3 c;
+__device__ __forceinline__ void mul_add(const M3 &a, const M3 &b, M3 &c) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      double2 s = make_double2(0.0, 0.0);
+      double2 s = c.a[i * 3 + j];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const double2 x = DA ? ccj(a.a[k * 3 + i]) : a.a[i * 3 + k];
@@ -63,59 +67,93 @@ __device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
       }
       c.a[i * 3 + j] = s;
     }
+}
+
+template <bool DA, bool DB>
+__device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
+  M3 c;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.a[k] = make_double2(0.0, 0.0);
+  mul_add<DA, DB>(a, b, c);
   return c;
 }
 
 __device__ __forceinline__ double2 det3(const M3 &m) {
   const double2 *a = m.a;
-  const double2 t0 = csub(cm(a[4], a[8]), cm(a[5], a[7]));
-  const double2 t1 = csub(cm(a[5], a[6]), cm(a[3], a[8]));
-  const double2 t2 = csub(cm(a[3], a[7]), cm(a[4], a[6]));
-  return cadd(cadd(cm(a[0], t0), cm(a[1], t1)), cm(a[2], t2));
+  const double2 t0 = cdet2(a[4], a[8], a[5], a[7]);
+  const double2 t1 = cdet2(a[5], a[6], a[3], a[8]);
+  const double2 t2 = cdet2(a[3], a[7], a[4], a[6]);
+  return cfma(a[2], t2, cfma(a[1], t1, cm(a[0], t0)));
 }
 
 // P(X): scaled Newton polar iteration, then the determinant's phase removed.
+// One step is N = (g Y + (g Y)^-dag) / 2 = h Y + conj(C e) with C the cofactor
+// matrix of Y ((Y^-1)^dag = conj(C / det Y)), h = g / 2 and e = s conj(det Y),
+// s = 1 / (2 g |det Y|^2).  For Y = Q H (polar form) any positive g and s give
+// N = Q (g H + c H^-1) / 2, the same Q: the scaled steps take g ~ |det Y|^(-1/3)
+// and s = g^5 / 2 from FP32 arithmetic; the unscaled steps (g = 1) need s to
+// FP64 accuracy, since with c != 1 the iterates would converge to sqrt(c) Q.
 // Scaling while a step still changes Y by more than 1 % (relative); the
-// iteration stops after a step that changed it by less than 1e-12, which by
-// the quadratic convergence leaves Y within ~1e-24 of the polar factor.
+// iteration stops after an unscaled step that changed it by less than 1e-8:
+// near the fixed point such a step leaves an error of about half its square
+// (~5e-17, FP64 rounding).  The singular values of every iterate are >= 1
+// (those of (g H + c H^-1) / 2 are >= sqrt(g c), = 1 unscaled), so |N|_F^2 >= 3
+// and testing the squared step against 3 x (relative bound)^2 is never looser.
 __device__ M3 project_su3(const M3 &X) {
   M3 Y = X;
   bool scaled = true;
   for (int it = 0; it < 60; ++it) {
-    const double2 d = det3(Y);
-    const double ad = sqrt(d.x * d.x + d.y * d.y);
-    const double g = scaled ? cbrt(1.0 / ad) : 1.0;
-    // (g Y)^-dag = (1/g) adj(Y)^dag / conj(det Y): entry (i, j) = conj(cof_ij(Y)) / (g conj(det))
-    const double inv = 1.0 / (g * (d.x * d.x + d.y * d.y));
-    M3 N;
-    double diff = 0.0, nrm = 0.0;
+    double2 C[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
-        const double2 cof = csub(cm(Y.a[r0 * 3 + c0], Y.a[r1 * 3 + c1]), cm(Y.a[r0 * 3 + c1], Y.a[r1 * 3 + c0]));
-        // conj(cof) / conj(d) = conj(cof / d) = conj(cof conj(d)) / |d|^2
-        const double2 q = ccj(cm(cof, ccj(d)));
-        const double2 yid = make_double2(q.x * inv, q.y * inv);
-        const double2 n = make_double2(0.5 * (g * Y.a[i * 3 + j].x + yid.x), 0.5 * (g * Y.a[i * 3 + j].y + yid.y));
-        const double2 e = csub(n, Y.a[i * 3 + j]);
-        diff += e.x * e.x + e.y * e.y;
-        nrm += n.x * n.x + n.y * n.y;
-        N.a[i * 3 + j] = n;
+        C[i * 3 + j] = cdet2(Y.a[r0 * 3 + c0], Y.a[r1 * 3 + c1], Y.a[r0 * 3 + c1], Y.a[r1 * 3 + c0]);
       }
-    Y = N;
-    if (!scaled && diff <= 1e-24 * nrm) break;
-    if (diff <= 1e-4 * nrm) scaled = false;
+    const double2 d = cfma(Y.a[2], C[2], cfma(Y.a[1], C[1], cm(Y.a[0], C[0])));
+    const double dd = __fma_rn(d.x, d.x, d.y * d.y);
+    double h, sc;
+    if (scaled) {
+      // g = |det Y|^(-1/3) = dd^(-1/6)
+      const double g = (dd > 1e-30 && dd < 1e30) ? (double)sqrtf(rcbrtf((float)dd)) : sqrt(rcbrt(dd));
+      const double g2 = g * g;
+      h = 0.5 * g;
+      sc = 0.5 * (g2 * g2 * g);
+    } else {
+      h = 0.5;
+      sc = 0.5 / dd;
+    }
+    const double2 e = make_double2(sc * d.x, -sc * d.y);
+    double diff = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double2 c = C[k], y = Y.a[k];
+      const double2 n = make_double2(__fma_rn(c.x, e.x, __fma_rn(-c.y, e.y, h * y.x)),
+                                     __fma_rn(-c.x, e.y, __fma_rn(-c.y, e.x, h * y.y)));
+      const double ex = n.x - y.x, ey = n.y - y.y;
+      diff = __fma_rn(ex, ex, __fma_rn(ey, ey, diff));
+      Y.a[k] = n;
+    }
+    if (!scaled && diff <= 3e-16) break;
+    if (diff <= 3e-4) scaled = false;
   }
+  // z = exp(-i arg(det Y) / 3), principal branch: an FP32 estimate (the branch
+  // follows the sign of Im det, kept by the conversion), then two Newton steps
+  // on z^3 det Y = 1 in FP64, z <- z (4 - z^3 det Y) / 3 (the residual
+  // w - 1 becomes -(2/3)(w - 1)^2 + O((w - 1)^3): 1e-7 -> 1e-14 -> rounding)
   const double2 d = det3(Y);
-  const double ph = atan2(d.y, d.x) / 3.0;
-  double sn, cs;
-  sincos(ph, &sn, &cs);
-  const double2 rot = make_double2(cs, -sn);
+  float sf, cf;
+  sincosf(atan2f((float)d.y, (float)d.x) / 3.0f, &sf, &cf);
+  double2 z = make_double2((double)cf, -(double)sf);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double2 w = cm(cm(cm(z, z), z), d);
+    z = cm(z, make_double2((4.0 - w.x) * (1.0 / 3.0), -w.y * (1.0 / 3.0)));
+  }
   M3 W;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) W.a[k] = cm(Y.a[k], rot);
+  for (int k = 0; k < 9; ++k) W.a[k] = cm(Y.a[k], z);
   return W;
 }
 
@@ -162,9 +200,7 @@ __device__ __forceinline__ void staples(const Lat &g, const int (&x)[4], long lo
     const M3 b = ld(B.at(mu, db, lexs(g, x, d, 1)));
     const M3 c = ld(A.at(d, da, lexs(g, x, mu, 1)));
     const M3 t = mul<false, false>(a, b);
-    const M3 s = mul<false, true>(t, c);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+    mul_add<false, true>(t, c, acc);
   }
   // - d: A_d(x-d)^dag B_mu(x-d) A_d(x-d+mu)
   {
@@ -173,9 +209,7 @@ __device__ __forceinline__ void staples(const Lat &g, const int (&x)[4], long lo
     const M3 b = ld(B.at(mu, db, xm));
     const M3 c = ld(A.at(d, da, lexs(g, x, d, -1, mu, 1)));
     const M3 t = mul<true, false>(a, b);
-    const M3 s = mul<false, false>(t, c);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+    mul_add<false, false>(t, c, acc);
   }
 }
 
@@ -244,9 +278,7 @@ __global__ void k_hyp3(Lat g, const double2 *U, const double2 *Vt, double a1, do
       const M3 a = ld(vt.at(nu, mu, i));
       const M3 b = ld(vt.at(mu, nu, lexs(g, x, nu, 1)));
       const M3 c = ld(vt.at(nu, mu, lexs(g, x, mu, 1)));
-      const M3 s = mul<false, true>(mul<false, false>(a, b), c);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+      mul_add<false, true>(mul<false, false>(a, b), c, acc);
     }
     // - nu
     {
@@ -254,9 +286,7 @@ __global__ void k_hyp3(Lat g, const double2 *U, const double2 *Vt, double a1, do
       const M3 a = ld(vt.at(nu, mu, xm));
       const M3 b = ld(vt.at(mu, nu, xm));
       const M3 c = ld(vt.at(nu, mu, lexs(g, x, nu, -1, mu, 1)));
-      const M3 s = mul<false, false>(mul<true, false>(a, b), c);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc.a[k] = cadd(acc.a[k], s.a[k]);
+      mul_add<false, false>(mul<true, false>(a, b), c, acc);
     }
   }
   double2 u[9];
