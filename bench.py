@@ -567,13 +567,17 @@ def run_ours(args):
     # the two CG kernels, timed alternately as the iteration runs them (CUDA
     # events between launches); the roofline is reported for the slower one
     hbm, peak_kind = peaks()
+    # the key names the workload the kernels ran: a capture's traffic stands only
+    # for the same kernels on the same lattice and number of systems
     tag = f"{args.precision}{'_r12' if args.links == 'recon12' else ''}_{'x'.join(map(str, L))}"
+    if nsys > 1:
+        tag += f"_{nsys}sys_{form['kernels']}"
     kern = []
     for kk, what in ((0, "t = D_oe r + beta t_old, |t|^2"),
                      (1, "p = r + beta p; r -= alpha (4m^2 p - D_eo t); x += alpha p; |r|^2, Re<r,p>")):
         ms_k, by_k = ctx.time_cg_kernel(kk, prec, nlaunch=100)
-        kern.append({"kernel": f"k_dslash CG kernel {kk + 1}: {what} ({args.precision}, links {args.links}, "
-                               f"{nrhs} RHS)",
+        kern.append({"kernel": f"{form['kernels']} CG kernel {kk + 1}: {what} ({args.precision}, links {args.links}, "
+                               f"{nsys} systems)",
                      "key": f"cg_k{kk + 1}_{tag}", "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": by_k,
                      "achieved": by_k / (ms_k * 1e-3) / 1e9})
     dom = max(kern, key=lambda d: d["ms_per_launch"])
