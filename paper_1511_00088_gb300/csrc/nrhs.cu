@@ -7,13 +7,16 @@
 // contiguous block) and SL threads per site.  Per chunk:
 //   * one bulk copy (cp.async.bulk, mbarrier completion, bounded wait) brings
 //     the tile's links into shared memory, the next tile's copy in flight
-//     while this one is computed (two stages); with reconstruct-12 the block
-//     first rebuilds row 2 of every link once into a full 3x3 copy;
+//     while this one is computed (two stages);
 //   * each thread computes its site's coordinates, neighbour indices and
-//     staggered/boundary signs once, then loops over the systems j = lane,
-//     lane + SL, ...: it gathers the 8 neighbour vectors of system j, applies
-//     the links from shared memory and runs the system's epilogue with its
-//     own alpha, beta, 4 m^2 (states read once per launch into shared memory).
+//     staggered/boundary signs once; with reconstruct-12 (and in the
+//     one-stage form) the block then writes a full 3x3 copy of every link
+//     once, row 2 rebuilt, the hop's sign folded in and the backward links
+//     stored daggered, so that all 8 hops are one product form;
+//   * the thread loops over the systems j = lane, lane + SL, ...: it gathers
+//     the 8 neighbour vectors of system j, applies the links from shared
+//     memory and runs the system's epilogue with its own alpha, beta, 4 m^2
+//     (states read once per launch into shared memory).
 // The links and the index arithmetic are so paid once per chunk instead of
 // once per system (the one-system-per-block form reloads them, from L2, for
 // every system).  FP32 links and vectors; epilogues EPI_CG_K1R and EPI_CG_K2
@@ -26,12 +29,14 @@ namespace stag {
 
 constexpr int NRHS_MAX = 64;  // systems per launch
 
-// The SU(3) x colour-vector products on Blackwell's packed FP32x2 FMA: with
-// v_b = (re, im) and w_b = (-im, re), a complex multiply-accumulate is
+// The SU(3) x colour-vector products on Blackwell's packed FP32x2 FMA.  On the
+// stored links (plain links, two stages, no full copy), with v_b = (re, im)
+// and w_b = (-im, re), a complex multiply-accumulate is
 //   h += Re(U_ab) v_b + Im(U_ab) w_b                      (U v)
 //   h += Re(U_ba) v_b - Im(U_ba) w_b                      (U^dag v)
-// two packed FMAs instead of four scalar ones (the links come from shared
-// memory as (re, im) pairs, the vectors are held as pairs).
+// two packed FMAs instead of four scalar ones, then acc += sign h.  On the full
+// copy (signs and daggers folded in) mv_split below needs no sign step and
+// no w_b.
 __device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
 
 // acc += sgn U v
@@ -67,6 +72,25 @@ __device__ __forceinline__ void mvdag_x2(const float2 *u, int ls, const float2 (
       h = __ffma2_rn(bc2(e.y), w[b], h);
     }
     acc[a] = __ffma2_rn(bc2(sgn), h, acc[a]);
+  }
+}
+
+// acc1 += U (Re v), acc2 += U (Im v), element pairs (Re U_ab, Im U_ab) times
+// the broadcast real / imaginary part of v_b: (U v)_a = (acc1.x - acc2.y,
+// acc1.y + acc2.x).  The links of the block's full copy already carry the
+// site's staggered sign and, for the backward hops, the dagger, so every hop is
+// this one form and the two sums combine once per site and system.
+__device__ __forceinline__ void mv_split(const float2 *u, int ls, const float2 (&v)[3], float2 (&acc1)[3],
+                                         float2 (&acc2)[3]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float2 vr = bc2(v[b].x), vi = bc2(v[b].y);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 e = u[(3 * a + b) * ls];
+      acc1[a] = __ffma2_rn(e, vr, acc1[a]);
+      acc2[a] = __ffma2_rn(e, vi, acc2[a]);
+    }
   }
 }
 
@@ -120,6 +144,7 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   __shared__ volatile int failed;
   __shared__ SysF sf32[NRHS_MAX];
   __shared__ float red[NRHS_MAX][NW][NV];
+  __shared__ float hop_sgn[EXPAND ? 8 : 1][LT];  // the signs the full copy folds in
   const Geom g = a.g;
   const int Ve = g.Ve, P = a.par_out, nsys = a.nsys;
   const int tid = threadIdx.x, i = tid % LT, lane = tid / LT, warp = tid >> 5;
@@ -163,45 +188,8 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
       failed = 1;
       if (a.ctl.flags != nullptr) atomicExch(a.ctl.flags + 4, 1);
     }
-    const float2 *L = stg;
-    constexpr int LNE = EXPAND ? 9 : NEL;  // elements per link in the copy the compute reads
-    if (EXPAND) {
-      __syncthreads();  // every thread is done with last round's full copy
-      // the full copy: stored elements, and (reconstruct-12) row 2 = conj(row0 x row1)
-      for (int k = tid; k < 8 * LT; k += BT) {
-        const int slot = k / LT, ii = k % LT;
-        const float2 *sp = stg + slot * (NEL * LT) + ii;
-        float2 *dp = full + slot * (9 * LT) + ii;
-        if (RECON) {
-          float2 r0[3], r1[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            r0[c] = sp[c * LT];
-            r1[c] = sp[(3 + c) * LT];
-            dp[c * LT] = r0[c];
-            dp[(3 + c) * LT] = r1[c];
-          }
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-            const float re =
-                (r0[c1].x * r1[c2].x - r0[c1].y * r1[c2].y) - (r0[c2].x * r1[c1].x - r0[c2].y * r1[c1].y);
-            const float im =
-                (r0[c1].x * r1[c2].y + r0[c1].y * r1[c2].x) - (r0[c2].x * r1[c1].y + r0[c2].y * r1[c1].x);
-            dp[(6 + c) * LT] = make_float2(re, -im);
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 9; ++e) dp[e * LT] = sp[e * LT];
-        }
-      }
-      L = full;
-    }
-    __syncthreads();  // this round's links ready; the stage the next copy fills is free
-    if (tid == 0 && !failed && round + 1 < nmine) {
-      fence_proxy_async_smem();
-      issue(round + 1);
-    }
+    // this thread's site: neighbour indices and the hop signs (staggered
+    // phase, antiperiodic t boundary; backward hops enter with a minus sign)
     const int s = t * LT + i;
     const bool valid = s < Ve;
     int sf[4], sb[4];
@@ -232,6 +220,54 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
         }
       }
     }
+    const float2 *L = stg;  // the stage itself (no full copy: plain links, two stages)
+    if (EXPAND) {
+      if (lane == 0) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          hop_sgn[mu][i] = valid ? bf[mu] : 0.f;
+          hop_sgn[4 + mu][i] = valid ? -bb[mu] : 0.f;
+        }
+      }
+      __syncthreads();  // every thread is done with last round's full copy; the signs are in
+      // the full copy: sign x link (forward hops), sign x link^dag (backward
+      // hops), with (reconstruct-12) row 2 = conj(row0 x row1) rebuilt first
+      for (int k = tid; k < 8 * LT; k += BT) {
+        const int slot = k / LT, ii = k % LT;
+        const float sg = hop_sgn[slot][ii];
+        const float2 *sp = stg + slot * (NEL * LT) + ii;
+        float2 *dp = full + slot * (9 * LT) + ii;
+        float2 m[9];
+#pragma unroll
+        for (int e = 0; e < NEL; ++e) m[e] = sp[e * LT];
+        if (RECON) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            const float2 *r0 = m, *r1 = m + 3;
+            const float re =
+                (r0[c1].x * r1[c2].x - r0[c1].y * r1[c2].y) - (r0[c2].x * r1[c1].x - r0[c2].y * r1[c1].y);
+            const float im =
+                (r0[c1].x * r1[c2].y + r0[c1].y * r1[c2].x) - (r0[c2].x * r1[c1].y + r0[c2].y * r1[c1].x);
+            m[6 + c] = make_float2(re, -im);
+          }
+        }
+        if (slot < 4) {
+#pragma unroll
+          for (int e = 0; e < 9; ++e) dp[e * LT] = make_float2(sg * m[e].x, sg * m[e].y);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) dp[(3 * a + b) * LT] = make_float2(sg * m[3 * b + a].x, -sg * m[3 * b + a].y);
+        }
+      }
+    }
+    __syncthreads();  // this round's links ready; the stage the next copy fills is free
+    if (tid == 0 && !failed && round + 1 < nmine) {
+      fence_proxy_async_smem();
+      issue(round + 1);
+    }
     for (int j = lane; j < nsys; j += SL) {
       const SysF S = sf32[j];
       if (!S.act) continue;  // uniform per warp
@@ -252,10 +288,21 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
           ld3_rw(a.out, j, s, Ve, c0);
         }
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (EXPAND) {
+          float2 acc2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-          mv_x2(L + mu * (LNE * LT) + i, LT, vf[mu], bf[mu], acc);
-          mvdag_x2(L + (4 + mu) * (LNE * LT) + i, LT, vb[mu], -bb[mu], acc);
+          for (int mu = 0; mu < 4; ++mu) {
+            mv_split(full + mu * (9 * LT) + i, LT, vf[mu], acc, acc2);
+            mv_split(full + (4 + mu) * (9 * LT) + i, LT, vb[mu], acc, acc2);
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[a] = make_float2(acc[a].x - acc2[a].y, acc[a].y + acc2[a].x);
+        } else {
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) {
+            mv_x2(L + mu * (NEL * LT) + i, LT, vf[mu], bf[mu], acc);
+            mvdag_x2(L + (4 + mu) * (NEL * LT) + i, LT, vb[mu], -bb[mu], acc);
+          }
         }
         if (EPI == EPI_CG_K2) {
           // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
