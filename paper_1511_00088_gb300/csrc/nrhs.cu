@@ -13,14 +13,16 @@
 //     one-stage form) the block then writes a full 3x3 copy of every link
 //     once, row 2 rebuilt, the hop's sign folded in and the backward links
 //     stored daggered, so that all 8 hops are one product form;
-//   * the thread loops over the systems j = lane, lane + SL, ...: it gathers
-//     the 8 neighbour vectors of system j, applies the links from shared
-//     memory and runs the system's epilogue with its own alpha, beta, 4 m^2
-//     (states read once per launch into shared memory).
+//   * the SL threads of a site (neighbours in one warp) share out the
+//     systems still iterating (compacted once per launch): each gathers the 8
+//     neighbour vectors of its system, applies the links from shared memory
+//     (one address per site, broadcast to its lanes) and runs the system's
+//     epilogue with its own alpha, beta, 4 m^2 (states read once per launch
+//     into shared memory).
 // The links and the index arithmetic are so paid once per chunk instead of
 // once per system (the one-system-per-block form reloads them, from L2, for
 // every system).  FP32 links and vectors; epilogues EPI_CG_K1R and EPI_CG_K2
-// as in k_dslash.  Reductions: per system a 32-lane tree per warp after each
+// as in k_dslash.  Reductions: per system a tree over the warp's sites after each
 // chunk, the warp sums in shared memory, one FP64 partial per system and
 // block at the end (k_finalize sums them).
 #include "launch.h"
@@ -144,10 +146,15 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   __shared__ volatile int failed;
   __shared__ SysF sf32[NRHS_MAX];
   __shared__ float red[NRHS_MAX][NW][NV];
+  __shared__ int act_list[NRHS_MAX];  // the systems this launch updates, in order
+  __shared__ int n_act;
   __shared__ float hop_sgn[EXPAND ? 8 : 1][LT];  // the signs the full copy folds in
   const Geom g = a.g;
   const int Ve = g.Ve, P = a.par_out, nsys = a.nsys;
-  const int tid = threadIdx.x, i = tid % LT, lane = tid / LT, warp = tid >> 5;
+  // the SL threads of a site are neighbours in one warp (a warp covers 32 / SL
+  // sites): a link element read from shared memory is one address per site,
+  // broadcast to the site's lanes
+  const int tid = threadIdx.x, i = tid / SL, lane = tid % SL, warp = tid >> 5;
   const int ntile = (Ve + LT - 1) / LT;
   const int nmine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   int issued = 0;  // thread 0: tiles whose copy was issued
@@ -180,6 +187,14 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   for (int k = tid; k < NRHS_MAX * NW * NV; k += BT) (&red[0][0][0])[k] = 0.f;
   if (tid == 0 && a.ctl.flags != nullptr && *(volatile int *)(a.ctl.flags + 4) != 0) failed = 1;
   __syncthreads();
+  // the active systems, compacted (read after the first round's barrier): the
+  // lanes of a warp then share out only systems that still iterate
+  if (tid == 0) {
+    int n = 0;
+    for (int j = 0; j < nsys; ++j)
+      if (sf32[j].act) act_list[n++] = j;
+    n_act = n;
+  }
 
   for (int round = 0; round < nmine; ++round) {
     const int t = (int)blockIdx.x + round * (int)gridDim.x;
@@ -268,12 +283,14 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
       fence_proxy_async_smem();
       issue(round + 1);
     }
-    for (int j = lane; j < nsys; j += SL) {
+    const int nact = n_act;
+    for (int k0 = 0; k0 < nact; k0 += SL) {  // uniform trip count: every lane shuffles
+      const bool has = k0 + lane < nact;
+      const int j = has ? act_list[k0 + lane] : 0;
       const SysF S = sf32[j];
-      if (!S.act) continue;  // uniform per warp
       const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
       float q0 = 0.f, q1 = 0.f;
-      if (valid) {
+      if (has && valid) {
         float2 vf[4][3], vb[4][3], c0[3], c1[3], c2[3];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
@@ -328,9 +345,13 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
           st3(a.out, j, s, Ve, c0);
         }
       }
-      q0 = warp_sum(q0);
-      if (NV > 1) q1 = warp_sum(q1);
-      if ((tid & 31) == 0) {
+      // sum over the warp's sites, lane by lane (one system per lane)
+#pragma unroll
+      for (int o = SL; o < 32; o <<= 1) {
+        q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+        if (NV > 1) q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+      }
+      if ((tid & 31) < SL && has) {
         red[j][warp][0] += q0;
         if (NV > 1) red[j][warp][NV - 1] += q1;
       }
@@ -343,13 +364,13 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
       for (int q = issued - STG > 0 ? issued - STG : 0; q < issued; ++q) mbar_wait(&bar[q % STG], (unsigned)(q / STG) & 1u);
     __syncthreads();
   }
-  // one FP64 partial per system and value: the warps of the system's lane in order
+  // one FP64 partial per system and value: the warps in order
   if (a.ctl.st != nullptr) {
     for (int k = tid; k < nsys * NV; k += BT) {
-      const int j = k / NV, v = k % NV, ln = j % SL;
+      const int j = k / NV, v = k % NV;
       float sum = 0.f;
 #pragma unroll
-      for (int w = 0; w < LT / 32; ++w) sum += red[j][ln * (LT / 32) + w][v];
+      for (int w = 0; w < NW; ++w) sum += red[j][w][v];
       a.ctl.partials[((long long)j * NVMAX + v) * a.ctl.pstride + blockIdx.x] = (double)sum;
     }
   }
