@@ -13,16 +13,15 @@
 //     one-stage form) the block then writes a full 3x3 copy of every link
 //     once, row 2 rebuilt, the hop's sign folded in and the backward links
 //     stored daggered, so that all 8 hops are one product form;
-//   * the SL threads of a site (neighbours in one warp) share out the
-//     systems still iterating (compacted once per launch): each gathers the 8
-//     neighbour vectors of its system, applies the links from shared memory
-//     (one address per site, broadcast to its lanes) and runs the system's
-//     epilogue with its own alpha, beta, 4 m^2 (states read once per launch
-//     into shared memory).
+//   * the SL lanes of a site (lane l: whole warps of 32 consecutive sites)
+//     share out the systems still iterating (compacted once per launch): each
+//     gathers the 8 neighbour vectors of its system, applies the links from
+//     shared memory and runs the system's epilogue with its own alpha, beta,
+//     4 m^2 (states read once per launch into shared memory).
 // The links and the index arithmetic are so paid once per chunk instead of
 // once per system (the one-system-per-block form reloads them, from L2, for
 // every system).  FP32 links and vectors; epilogues EPI_CG_K1R and EPI_CG_K2
-// as in k_dslash.  Reductions: per system a tree over the warp's sites after each
+// as in k_dslash.  Reductions: per system a 32-lane tree per warp after each
 // chunk, the warp sums in shared memory, one FP64 partial per system and
 // block at the end (k_finalize sums them).
 #include "launch.h"
@@ -151,10 +150,8 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   __shared__ float hop_sgn[EXPAND ? 8 : 1][LT];  // the signs the full copy folds in
   const Geom g = a.g;
   const int Ve = g.Ve, P = a.par_out, nsys = a.nsys;
-  // the SL threads of a site are neighbours in one warp (a warp covers 32 / SL
-  // sites): a link element read from shared memory is one address per site,
-  // broadcast to the site's lanes
-  const int tid = threadIdx.x, i = tid / SL, lane = tid % SL, warp = tid >> 5;
+  // lane l = threads [l LT, (l + 1) LT): whole warps, 32 consecutive sites each
+  const int tid = threadIdx.x, i = tid % LT, lane = tid / LT, warp = tid >> 5;
   const int ntile = (Ve + LT - 1) / LT;
   const int nmine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   int issued = 0;  // thread 0: tiles whose copy was issued
@@ -188,7 +185,8 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   if (tid == 0 && a.ctl.flags != nullptr && *(volatile int *)(a.ctl.flags + 4) != 0) failed = 1;
   __syncthreads();
   // the active systems, compacted (read after the first round's barrier): the
-  // lanes of a warp then share out only systems that still iterate
+  // lanes share out only systems that still iterate, so a lane whose systems
+  // converged first does not leave its warps idle while the others work
   if (tid == 0) {
     int n = 0;
     for (int j = 0; j < nsys; ++j)
@@ -284,8 +282,8 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
       issue(round + 1);
     }
     const int nact = n_act;
-    for (int k0 = 0; k0 < nact; k0 += SL) {  // uniform trip count: every lane shuffles
-      const bool has = k0 + lane < nact;
+    for (int k0 = 0; k0 < nact; k0 += SL) {
+      const bool has = k0 + lane < nact;  // uniform per warp
       const int j = has ? act_list[k0 + lane] : 0;
       const SysF S = sf32[j];
       const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
@@ -345,13 +343,9 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
           st3(a.out, j, s, Ve, c0);
         }
       }
-      // sum over the warp's sites, lane by lane (one system per lane)
-#pragma unroll
-      for (int o = SL; o < 32; o <<= 1) {
-        q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-        if (NV > 1) q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-      }
-      if ((tid & 31) < SL && has) {
+      q0 = warp_sum(q0);
+      if (NV > 1) q1 = warp_sum(q1);
+      if ((tid & 31) == 0 && has) {
         red[j][warp][0] += q0;
         if (NV > 1) red[j][warp][NV - 1] += q1;
       }
