@@ -10,7 +10,8 @@
 // One block per hypercube, 256 threads:
 //   * its 32 internal links into shared memory;
 //   * the path averages W(A, D) for A < D (W(D, A) = W(A, D)^dag, W(A, A) =
-//     1), level by level in n = |A xor D|, one thread per matrix element: a
+//     1), level by level in n = |A xor D| (a table of the pairs per level),
+//     one thread per matrix element: a
 //     path's last step is one of the differing directions mu, so
 //     W(A, D) = (1/n) sum_mu W(A, D xor mu) step(D xor mu -> D);
 //   * the spin-taste entries from the Clifford algebra: g_X g_Y = e(X, Y)
@@ -61,6 +62,31 @@ __device__ __forceinline__ double spin_taste(int S, int F, int A, int B) {
   return (double)s;
 }
 
+// the 120 corner pairs A < D of a hypercube, ordered by n = |A xor D|
+// (32, 48, 32, 8 pairs), and the offset of each level
+struct PairTable {
+  unsigned char a[120], d[120];
+  int off[5];
+};
+constexpr int popc4(int x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
+constexpr PairTable make_pairs() {
+  PairTable p{};
+  int k = 0;
+  for (int n = 1; n <= 4; ++n) {
+    p.off[n - 1] = k;
+    for (int A = 0; A < 16; ++A)
+      for (int D = A + 1; D < 16; ++D)
+        if (popc4(A ^ D) == n) {
+          p.a[k] = (unsigned char)A;
+          p.d[k] = (unsigned char)D;
+          ++k;
+        }
+  }
+  p.off[4] = k;
+  return p;
+}
+__constant__ PairTable c_pairs = make_pairs();
+
 struct NprArgs {
   int L[4], H[4];
   long long V;
@@ -75,6 +101,7 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
   __shared__ double2 W[256][9];      // W(A, D), index A * 16 + D
   __shared__ double2 fld[4][16][3];  // chibar1, chi2, chibar3, chi4 at the corners
   __shared__ double2 red[NPR_BT / 32];
+  __shared__ unsigned char pa[120], pd[120];
   const long long h = blockIdx.x;
   int zc[4];
   {
@@ -108,12 +135,16 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
     const int Y = k / 9, e = k % 9;
     W[Y * 17][e] = make_double2((e % 4 == 0) ? 1.0 : 0.0, 0.0);
   }
+  if (t < 120) {
+    pa[t] = c_pairs.a[t];
+    pd[t] = c_pairs.d[t];
+  }
   __syncthreads();
   for (int n = 1; n <= 4; ++n) {
-    for (int item = t; item < 256 * 9; item += NPR_BT) {
-      const int pr = item / 9, e = item % 9;
-      const int A = pr >> 4, D = pr & 15;
-      if (!(A < D && __popc(A ^ D) == n)) continue;
+    const int p0 = c_pairs.off[n - 1], nitem = (c_pairs.off[n] - p0) * 9;
+    for (int item = t; item < nitem; item += NPR_BT) {
+      const int pr = p0 + item / 9, e = item % 9;
+      const int A = pa[pr], D = pd[pr];
       const int i = e / 3, j = e % 3;
       if (n == 1) {  // one step: the link itself (forward) or its adjoint
         const int mu = __ffs(A ^ D) - 1;
@@ -137,7 +168,7 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
           s = zfma(w, st, s);
         }
       }
-      const double inv = 1.0 / n;
+      const double inv = n == 2 ? 0.5 : n == 3 ? 1.0 / 3.0 : 0.25;  // constants: no FP64 division
       W[A * 16 + D][e] = make_double2(s.x * inv, s.y * inv);
     }
     __syncthreads();
