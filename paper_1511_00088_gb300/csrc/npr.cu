@@ -8,12 +8,12 @@
 //   U_AD(z) = the average over the shortest paths from z_A to z_D inside the
 //   hypercube of the link products (U_mu for +mu, U_mu^dag for -mu).
 // One block per hypercube, 256 threads:
-//   * its 32 internal links into shared memory;
-//   * the path averages W(A, D) for A < D (W(D, A) = W(A, D)^dag, W(A, A) =
-//     1), level by level in n = |A xor D| (a table of the pairs per level),
-//     one thread per matrix element: a
+//   * the path averages W(A, D) in shared memory, both orientations (W(D, A) =
+//     W(A, D)^dag, so that no read conjugates), W(A, A) = 1: level n = 1 is
+//     the hypercube's 32 internal links; levels n = |A xor D| = 2, 3, 4 (a
+//     table of the pairs A < D per level), one thread per matrix element: a
 //     path's last step is one of the differing directions mu, so
-//     W(A, D) = (1/n) sum_mu W(A, D xor mu) step(D xor mu -> D);
+//     W(A, D) = (1/n) sum_mu W(A, D xor mu) W(D xor mu, D);
 //   * the spin-taste entries from the Clifford algebra: g_X g_Y = e(X, Y)
 //     g_{X xor Y} with e(X, Y) = (-1)^(sum_{mu > nu} X_mu Y_nu), g_A^dag =
 //     (-1)^(n(n-1)/2) g_A (n set bits), so (g_S x x_F)_AB is nonzero only for
@@ -50,11 +50,6 @@ __device__ __forceinline__ int mul_sign(int X, int Y) {
     if ((Y >> nu) & 1) cnt += __popc(X >> (nu + 1));
   return (cnt & 1) ? -1 : 1;
 }
-// slot of the internal link (Y, mu), Y_mu = 0: mu * 8 + Y with bit mu removed
-__device__ __forceinline__ int lslot(int Y, int mu) {
-  return mu * 8 + ((Y & ((1 << mu) - 1)) | ((Y >> (mu + 1)) << mu));
-}
-
 // (g_S x x_F)_AB (real: 0 or +-1)
 __device__ __forceinline__ double spin_taste(int S, int F, int A, int B) {
   if ((A ^ S ^ B ^ F) != 0) return 0.0;
@@ -97,8 +92,7 @@ struct NprArgs {
 };
 
 __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
-  __shared__ double2 lk[32][9];      // U_mu(z_Y) for Y_mu = 0, slot lslot(Y, mu)
-  __shared__ double2 W[256][9];      // W(A, D), index A * 16 + D
+  __shared__ double2 W[256][9];      // W(A, D), index A * 16 + D, both orientations
   __shared__ double2 fld[4][16][3];  // chibar1, chi2, chibar3, chi4 at the corners
   __shared__ double2 red[NPR_BT / 32];
   __shared__ unsigned char pa[120], pd[120];
@@ -119,18 +113,20 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
     return x0 + (long long)a.L[0] * (x1 + (long long)a.L[1] * (x2 + (long long)a.L[2] * x3));
   };
   const int t = threadIdx.x;
-  // links and fields of the hypercube
-  for (int k = t; k < 16 * 4 * 9; k += NPR_BT) {
-    const int Y = k / 36, mu = (k / 9) % 4, e = k % 9;
-    if (!((Y >> mu) & 1)) lk[lslot(Y, mu)][e] = a.U[((long long)mu * a.V + site(Y)) * 9 + e];
+  // level n = 1, the hypercube's 32 internal links: W(A, D) = U_mu(z_A) for
+  // D = A + mu (A_mu = 0), W(D, A) its adjoint; level 0: W(A, A) = 1
+  for (int k = t; k < 32 * 9; k += NPR_BT) {
+    const int l = k / 9, e = k % 9, mu = l / 8, y = l % 8;
+    const int A = ((y >> mu) << (mu + 1)) | (y & ((1 << mu) - 1)), D = A | (1 << mu);
+    const double2 u = a.U[((long long)mu * a.V + site(A)) * 9 + e];
+    W[A * 16 + D][e] = u;
+    W[D * 16 + A][(e % 3) * 3 + e / 3] = make_double2(u.x, -u.y);
   }
   for (int k = t; k < 4 * 16 * 3; k += NPR_BT) {
     const int f = k / 48, A = (k / 3) % 16, c = k % 3;
     const double2 *src = f == 0 ? a.cb1 : f == 1 ? a.c2 : f == 2 ? a.cb3 : a.c4;
     fld[f][A][c] = src[site(A) * 3 + c];
   }
-  // W(A, A) = 1; the pairs A < D level by level in n = |A xor D|, one thread
-  // per (pair, element); W(D, A) = W(A, D)^dag is read from the A < D entry
   for (int k = t; k < 16 * 9; k += NPR_BT) {
     const int Y = k / 9, e = k % 9;
     W[Y * 17][e] = make_double2((e % 4 == 0) ? 1.0 : 0.0, 0.0);
@@ -140,36 +136,28 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
     pd[t] = c_pairs.d[t];
   }
   __syncthreads();
-  for (int n = 1; n <= 4; ++n) {
+  // levels n = 2, 3, 4, the pairs A < D from the table: the last step of a
+  // path is one of the differing directions mu, from P = D xor mu, so
+  // W(A, D) = (1/n) sum_mu W(A, P) W(P, D) (W(P, D): a link or its adjoint);
+  // one thread per matrix element, which also writes the adjoint entry
+  for (int n = 2; n <= 4; ++n) {
     const int p0 = c_pairs.off[n - 1], nitem = (c_pairs.off[n] - p0) * 9;
     for (int item = t; item < nitem; item += NPR_BT) {
       const int pr = p0 + item / 9, e = item % 9;
       const int A = pa[pr], D = pd[pr];
       const int i = e / 3, j = e % 3;
-      if (n == 1) {  // one step: the link itself (forward) or its adjoint
-        const int mu = __ffs(A ^ D) - 1;
-        const bool fwd = (D >> mu) & 1;
-        const double2 *u = fwd ? lk[lslot(A, mu)] : lk[lslot(D, mu)];
-        W[A * 16 + D][e] = fwd ? u[i * 3 + j] : make_double2(u[j * 3 + i].x, -u[j * 3 + i].y);
-        continue;
-      }
       double2 s = make_double2(0.0, 0.0);
       for (int mu = 0; mu < 4; ++mu) {
         if (!(((A ^ D) >> mu) & 1)) continue;
-        const int P = D ^ (1 << mu);  // the corner before the last step
-        const bool fwd = (D >> mu) & 1;  // +mu from P to D: U_mu(z_P); else -mu: U_mu(z_D)^dag
-        const double2 *u = fwd ? lk[lslot(P, mu)] : lk[lslot(D, mu)];
+        const int P = D ^ (1 << mu);
+        const double2 *wa = W[A * 16 + P], *wb = W[P * 16 + D];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          // W(A, P)[i][k], from the stored A <= P or P < A entry
-          const double2 w = (A <= P) ? W[A * 16 + P][i * 3 + k]
-                                     : make_double2(W[P * 16 + A][k * 3 + i].x, -W[P * 16 + A][k * 3 + i].y);
-          const double2 st = fwd ? u[k * 3 + j] : make_double2(u[j * 3 + k].x, -u[j * 3 + k].y);
-          s = zfma(w, st, s);
-        }
+        for (int k = 0; k < 3; ++k) s = zfma(wa[i * 3 + k], wb[k * 3 + j], s);
       }
       const double inv = n == 2 ? 0.5 : n == 3 ? 1.0 / 3.0 : 0.25;  // constants: no FP64 division
-      W[A * 16 + D][e] = make_double2(s.x * inv, s.y * inv);
+      s = make_double2(s.x * inv, s.y * inv);
+      W[A * 16 + D][e] = s;
+      W[D * 16 + A][j * 3 + i] = make_double2(s.x, -s.y);
     }
     __syncthreads();
   }
@@ -179,10 +167,7 @@ __global__ void __launch_bounds__(NPR_BT) k_npr(const NprArgs a) {
   const double s = spin_taste(a.S1, a.F1, A, B) * spin_taste(a.S2, a.F2, C, Dd);
   double2 t1 = make_double2(0.0, 0.0), t2 = make_double2(0.0, 0.0);
   {
-    // element (i, j) of W(X, Y) from the stored X <= Y entry (adjoint otherwise)
-    auto wget = [&](int X, int Y, int i, int j) -> double2 {
-      return X <= Y ? W[X * 16 + Y][i * 3 + j] : make_double2(W[Y * 16 + X][j * 3 + i].x, -W[Y * 16 + X][j * 3 + i].y);
-    };
+    auto wget = [&](int X, int Y, int i, int j) -> double2 { return W[X * 16 + Y][i * 3 + j]; };
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       double2 v1 = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
