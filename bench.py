@@ -12,9 +12,12 @@ Printed (rank 0, one JSON line):
               L2 flushed (256 MiB write) before every timed solve;
   e2e         the same metric through the C ABI with the source in pinned host
               memory and the solution copied back, copies inside the timing;
-  roofline    the dominant kernel (the FP32 half operator D_oe) against the
-              measured HBM copy bandwidth;
-  cpu_baseline the FP64 CPU oracle's CG on a bounded sample of the workload.
+  roofline    the slower of the two CG kernels against the measured HBM copy
+              bandwidth (and, in `nominal`, against ~8 TB/s);
+  cpu_baseline the FP64 CPU oracle's CG on a bounded sample of the workload
+              (all cores and one thread), and in `configs` the oracle on the
+              other configurations (full CGs on 8^4 and 16^3x32, operator
+              timings, an extrapolated 48^3x96 solve).
 Extra keys give time-to-solution of the mixed, FP16/BF16-storage and plain FP64
 solves on the same GPU.
 
@@ -25,6 +28,7 @@ scaling); no data-path collective.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import math
@@ -43,6 +47,7 @@ METRIC = "Dslash GFLOP/s & HBM GB/s; CG time-to-1e-10 residual, mixed/batched vs
 FLOP_PER_SITE_ITER = 1212     # 2 x 570 (two half operators) + 12 (mass) + 5 x 12 (BLAS-1)
 DSLASH_FLOP_PER_SITE = 570    # 8 x 66 (SU(3) x vector) + 7 x 6 (accumulation)
 PAPER_TX_CG_GFLOPS = 107.7    # Titan X, mixed CG, 20^3 x 64, one GPU (Table 2 of the paper)
+HBM_NOMINAL_GBS = 8000.0      # nominal HBM3e bandwidth (~8 TB/s); the roofline's peak is the measured copy
 L2_FLUSH_BYTES = 256 << 20
 # NPR contraction per hypercube, as the kernel computes it: the 120 path
 # averages W(A, D), A < D (the rest are adjoints or 1), at |A xor D| = n from n
@@ -273,6 +278,79 @@ def cpu_oracle_sample(L, U, b, mass, budget_s, threads=1):
     # the oracle also recomputes the true residual once (one more operator application)
     gflops = FLOP_PER_SITE_ITER * Ve * it / dt / 1e9
     return gflops, it, dt, used
+
+
+def cpu_oracle_configs(fp64_iters_48x96):
+    """The FP64 CPU oracle on the machine's host cores, per configuration: a full
+    CG on 8^4 (one thread and all cores), the half operator and M^dag M on
+    20^3x64, a full CG on 16^3x32 (m = 0.02, all cores), and on 48^3x96 one
+    M^dag M plus 10 CG iterations, extrapolated to a whole solve by the GPU FP64
+    solve's iteration count (a full CPU solve there would take hours).  A
+    baseline only: the oracle is plain, untuned code."""
+    import oracle
+    import torch
+
+    from paper_1511_00088_gb300 import synth
+    out = {}
+
+    def cg_run(L, U, b, m, tol=1e-10, maxiter=100000):
+        t = time.perf_counter()
+        _, st, it, _ = oracle.cg(L, U, m, b, tol=tol, maxiter=maxiter)
+        dt = time.perf_counter() - t
+        Ve = synth.volume(L) // 2
+        return {"s": dt, "iters": int(it), "GFLOP/s": FLOP_PER_SITE_ITER * Ve * it / dt / 1e9}
+
+    with oracle.threads(0) as th:
+        cores = th.count()
+    L = (8, 8, 8, 8)
+    U = synth.random_links(L, 0.3, synth.seed_for(0, 1))
+    b = synth.gaussian_vector(synth.volume(L) // 2, synth.seed_for(0, 2))
+    c0 = {"one_thread": cg_run(L, U, b, 0.05)}
+    with oracle.threads(0):
+        c0["all_cores"] = cg_run(L, U, b, 0.05)
+    out["config0_8^4_m0.05_fp64_cg_to_1e-10"] = c0
+    L = (20, 20, 20, 64)
+    Ve = synth.volume(L) // 2
+    U = synth.random_links(L, 0.4, synth.seed_for(1, 1))
+    b = synth.gaussian_vector(Ve, synth.seed_for(1, 2))
+    c1 = {}
+    for label, n in (("one_thread", 1), ("all_cores", 0)):
+        with oracle.threads(n) if n != 1 else contextlib.nullcontext():
+            t = time.perf_counter()
+            oracle.dslash_oe(L, U, b)
+            t1 = time.perf_counter() - t
+            t = time.perf_counter()
+            oracle.mdagm(L, U, 0.01, b)
+            t2 = time.perf_counter() - t
+        c1[label] = {"dslash_oe_ms": 1e3 * t1, "dslash_oe_GFLOP/s": 570 * Ve / t1 / 1e9,
+                     "mdagm_ms": 1e3 * t2, "mdagm_GFLOP/s": (2 * 570 + 12) * Ve / t2 / 1e9}
+    out["config1_20^3x64_operator"] = c1
+    L = (16, 16, 16, 32)
+    U = synth.random_links(L, 0.4, synth.seed_for(3, 1))
+    b = synth.gaussian_vector(synth.volume(L) // 2, synth.seed_for(3, 2))
+    with oracle.threads(0):
+        out["config3_16^3x32_m0.02_fp64_cg_to_1e-10"] = {"all_cores": cg_run(L, U, b, 0.02)}
+    if fp64_iters_48x96:
+        L = (48, 48, 48, 96)
+        Ve = synth.volume(L) // 2
+        Ud = synth.random_links_device(L, 0.4, synth.seed_for(4, 1), device="cuda")
+        U = Ud.cpu().numpy()
+        del Ud
+        torch.cuda.empty_cache()
+        b = synth.gaussian_vector(Ve, synth.seed_for(4, 2))
+        with oracle.threads(0):
+            t = time.perf_counter()
+            oracle.mdagm(L, U, 0.005, b)
+            t_m = time.perf_counter() - t
+            r10 = cg_run(L, U, b, 0.005, tol=1e-300, maxiter=10)
+        per_it = r10["s"] / max(r10["iters"], 1)
+        out["config4_48^3x96_m0.005"] = {
+            "all_cores": {"mdagm_s": t_m, "cg_10_iterations_s": r10["s"], "GFLOP/s": r10["GFLOP/s"]},
+            "extrapolated_one_source_s": per_it * fp64_iters_48x96,
+            "extrapolated_16_sources_s": 16 * per_it * fp64_iters_48x96,
+            "iterations_used": fp64_iters_48x96}
+        del U
+    return out, cores
 
 
 def timed_solve(ctx, srcs, masses, prec, tol, maxiter, stream):
@@ -585,6 +663,8 @@ def run_ours(args):
     traffic = ncu_traffic(dom["key"])
     roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s",
             "frac": dom["achieved"] / hbm, "traffic": traffic, "peak_source": peak_kind,
+            # the nominal figure (~8 TB/s HBM3e) beside the measured copy peak
+            "nominal": {"peak": HBM_NOMINAL_GBS, "frac": dom["achieved"] / HBM_NOMINAL_GBS},
             # the ncu DRAM bytes of one launch over its live time: the DRAM side
             # of the effective (algorithmic) fraction, the rest being L2 hits
             "dram_gbs": traffic / (dom["ms_per_launch"] * 1e-3) / 1e9 if traffic else None,
@@ -643,6 +723,9 @@ def run_ours(args):
                          f"({dt:.1f} s, {used} threads: the operator's per-site loop in parallel)",
                "single_thread": {"value": g1, "unit": "GFLOP/s", "cores": 1,
                                  "sample": f"{it1} FP64 CG iterations ({dt1:.1f} s, one thread)"}}
+        if "batched" in extras:
+            c4 = extras["batched"].get("config4_48x96_16src_m0.005", {}).get("fp64_one_source", {})
+            cpu["configs"], _ = cpu_oracle_configs(c4.get("iters_max"))
 
     if rank == 0:
         line = {
