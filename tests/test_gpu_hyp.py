@@ -56,3 +56,18 @@ def test_unit_field_and_cg_on_smeared_links():
     assert np.abs(Hh - oracle.hyp(L, U)).max() <= 1e-13
     t = oracle.true_residual(L, Hh, 0.02, b, xs[0])
     assert t <= 1e-10 and abs(t - tr[0]) <= 1e-12 + 0.05 * t
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1e6])
+def test_hyp_of_scaled_links(scale):
+    """The projection's polar factor is scale-invariant: links scaled by 1e-6 or
+    1e6 (|det|^2 of the first-level sums near 1e-36 or 1e108, outside the range
+    where the determinant scale comes from FP32 arithmetic, so its FP64 branch
+    runs) smear to the oracle's links within the same bound."""
+    L = (4, 2, 6, 8)
+    U = scale * synth.random_links(L, 0.4, 804)
+    ref = oracle.hyp(L, U)
+    with stag.Context(L) as ctx:
+        H = ctx.hyp_smear(U)
+    assert np.abs(H - ref).max() <= 1e-13
+    assert np.abs(H @ np.conj(np.swapaxes(H, -1, -2)) - np.eye(3)).max() < 1e-14
