@@ -87,3 +87,23 @@ def test_nrhs_form_48_systems_production_lattice():
         r, k = divmod(j, len(masses))
         t = oracle.true_residual(L, U, masses[k], bs[r], xs[j].cpu().numpy())
         assert t <= 1e-10, (j, t)
+
+
+@pytest.mark.parametrize("nsrc,masses", [(16, [0.05, 0.07, 0.1, 0.2]), (13, [0.05, 0.07, 0.1, 0.15, 0.2])])
+def test_nrhs_at_and_beyond_max_systems(nsrc, masses):
+    """64 systems, the most this form takes (one shared-memory slot per
+    system), run in it; 65 systems fall back to another form: every system's
+    true residual by the oracle <= 1e-10 in both."""
+    L = (4, 4, 4, 8)
+    V = synth.volume(L)
+    U = synth.random_links(L, 0.4, 711)
+    bs = [synth.gaussian_vector(V // 2, 712 + r) for r in range(nsrc)]
+    xs, st, it, tr, form = solve_forced(L, U, bs, masses, True, 4)
+    assert st == stag.STAG_OK
+    nsys = nsrc * len(masses)
+    assert (form["kernels"] == "k_cg_nrhs") == (nsys <= 64), form
+    for j in range(nsys):
+        r, k = divmod(j, len(masses))
+        t = oracle.true_residual(L, U, masses[k], bs[r], xs[j])
+        assert t <= 1e-10, (j, t)
+        assert abs(t - tr[j]) <= 1e-12 + 0.05 * t
