@@ -326,7 +326,8 @@ int stag_solve_counters(const stag_ctx *ctx, int *loop_passes, int *update_steps
  * share each chunk's links in shared memory among the out[0] systems of a
  * block (one warp per system), 2 when every block runs every system on
  * links staged once per tile in shared memory (out[0] = the systems,
- * out[2] = out[3] = threads per site).  Implementation detail of this
+ * out[2] = out[3] = threads per site), 3 the same with the first kernel
+ * taking two systems per pass through each thread.  Implementation detail of this
  * library (the paper has no counterpart), for reports.  STAG_ERR_ARG before
  * the first solve.
  */

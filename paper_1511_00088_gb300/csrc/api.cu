@@ -867,15 +867,17 @@ int work_prepare(stag_ctx *c, int nsys, int precision, int ms = 0) {
     if (nrhs_ok && !(fns && fns[0] != 0) && !(fmr && fmr[0] != 0)) {
       cands.push_back(202);
       cands.push_back(204);
+      if (recon) cands.push_back(224);
     }
     // STAG_NRHS = 2 or 4: this form with that many threads per site (two link
     // stages), 14: 4 threads per site with one stage (3 blocks per SM; measured
     // slower: 48-system 20^3 x 64 solve 3.34 s vs 2.36 s, so not a default
-    // candidate); 0: never this form
+    // candidate), 24: kernel 1 with two systems per pass through the thread
+    // (reconstruct-12 links; kernel 2 as form 4); 0: never this form
     const char *fnr = getenv("STAG_NRHS");
     if (fnr && nrhs_ok) {
       const int f = atoi(fnr);
-      if (f == 2 || f == 4 || f == 14) cands.assign(1, 200 + f);
+      if (f == 2 || f == 4 || f == 14 || (f == 24 && recon)) cands.assign(1, 200 + f);
     }
     if (fnr && fnr[0] == '0' && fnr[1] == 0) {
       std::vector<int> keep;
@@ -2326,7 +2328,7 @@ int stag_solve_form(const stag_ctx *c, int out[8]) {
   out[4] = w.tma;
   out[5] = w.l2p;
   out[6] = solve_unroll();
-  out[7] = w.mrhs ? 1 : (w.nrhs_sl ? 2 : 0);
+  out[7] = w.mrhs ? 1 : (w.nrhs_sl == 24 ? 3 : (w.nrhs_sl ? 2 : 0));
   if (w.nrhs_sl) {
     out[0] = w.nsys;  // every system in every block
     out[1] = 1;

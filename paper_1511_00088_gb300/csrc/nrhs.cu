@@ -15,9 +15,10 @@
 //     stored daggered, so that all 8 hops are one product form;
 //   * the SL lanes of a site (lane l: whole warps of 32 consecutive sites)
 //     share out the systems still iterating (compacted once per launch): each
-//     gathers the 8 neighbour vectors of its system, applies the links from
-//     shared memory and runs the system's epilogue with its own alpha, beta,
-//     4 m^2 (states read once per launch into shared memory).
+//     gathers the 8 neighbour vectors of its system (or, JJ = 2, of two
+//     systems in two phases), applies the links from shared memory and runs
+//     the system's epilogue with its own alpha, beta, 4 m^2 (states read once
+//     per launch into shared memory).
 // The links and the index arithmetic are so paid once per chunk instead of
 // once per system (the one-system-per-block form reloads them, from L2, for
 // every system).  FP32 links and vectors; epilogues EPI_CG_K1R and EPI_CG_K2
@@ -95,6 +96,24 @@ __device__ __forceinline__ void mv_split(const float2 *u, int ls, const float2 (
   }
 }
 
+// mv_split for two systems at once: each link element read from shared memory
+// serves both
+__device__ __forceinline__ void mv_split2(const float2 *u, int ls, const float2 (&va)[3], const float2 (&vb)[3],
+                                          float2 (&a1)[3], float2 (&a2)[3], float2 (&b1)[3], float2 (&b2)[3]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float2 vra = bc2(va[b].x), via = bc2(va[b].y), vrb = bc2(vb[b].x), vib = bc2(vb[b].y);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 e = u[(3 * a + b) * ls];
+      a1[a] = __ffma2_rn(e, vra, a1[a]);
+      a2[a] = __ffma2_rn(e, via, a2[a]);
+      b1[a] = __ffma2_rn(e, vrb, b1[a]);
+      b2[a] = __ffma2_rn(e, vib, b2[a]);
+    }
+  }
+}
+
 // the three colours of site s of system k (FP32 vector, read-only path)
 __device__ __forceinline__ void ld3(const VecArg &f, int k, int s, int Ve, float2 (&v)[3]) {
   const float2 *p = reinterpret_cast<const float2 *>(f.v) + (long long)k * f.sstr + s;
@@ -128,10 +147,15 @@ inline unsigned nrhs_smem_bytes(int recon, int stg) {
 // STG = 2: two stages, the next tile's copy in flight during the whole round
 // (2 blocks per SM); STG = 1: one stage, refilled as soon as this round's
 // links are in the full copy (less shared memory: 3 blocks per SM)
-template <int RECON, int EPI, int SL, int STG>
+// JJ = 2 (reconstruct-12 only): two systems per pass through the thread, in
+// two phases (the forward neighbours of both, then the backward ones, so that
+// as many loads are in flight as with one system), each link element read
+// from shared memory once for both systems
+template <int RECON, int EPI, int SL, int STG, int JJ>
 __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsArgs a) {
   static_assert(EPI == EPI_CG_K1R || EPI == EPI_CG_K2, "the two CG kernels");
   static_assert(STG == 1 || STG == 2, "one or two stages");
+  static_assert(JJ == 1 || (JJ == 2 && (RECON || STG == 1)), "two systems per pass need the full copy");
   constexpr int BT = LT * SL;
   constexpr int NW = BT / 32;
   constexpr int NEL = RECON ? 6 : 9;
@@ -282,72 +306,181 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
       issue(round + 1);
     }
     const int nact = n_act;
-    for (int k0 = 0; k0 < nact; k0 += SL) {
-      const bool has = k0 + lane < nact;  // uniform per warp
-      const int j = has ? act_list[k0 + lane] : 0;
-      const SysF S = sf32[j];
-      const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
-      float q0 = 0.f, q1 = 0.f;
-      if (has && valid) {
-        float2 vf[4][3], vb[4][3], c0[3], c1[3], c2[3];
+    if constexpr (JJ == 2) {
+      for (int k0 = 0; k0 < nact; k0 += 2 * SL) {
+        const int ka = k0 + 2 * lane;
+        const bool hasA = ka < nact, hasB = ka + 1 < nact;  // uniform per warp
+        const int ja = hasA ? act_list[ka] : 0, jb = hasB ? act_list[ka + 1] : 0;
+        float qa0 = 0.f, qa1 = 0.f, qb0 = 0.f, qb1 = 0.f;
+        if (hasA && valid) {
+          const float2 z = make_float2(0.f, 0.f);
+          float2 pa1[3] = {z, z, z}, pa2[3] = {z, z, z}, pb1[3] = {z, z, z}, pb2[3] = {z, z, z};
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-          ld3(a.in, j, sf[mu], Ve, vf[mu]);
-          ld3(a.in, j, sb[mu], Ve, vb[mu]);
+          for (int h = 0; h < 2; ++h) {  // forward hops, then backward hops
+            float2 va[4][3], vb2[4][3];
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+              const int nb = h == 0 ? sf[mu] : sb[mu];
+              ld3(a.in, ja, nb, Ve, va[mu]);
+              if (hasB) {
+                ld3(a.in, jb, nb, Ve, vb2[mu]);
+              } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) vb2[mu][c] = z;
+              }
+            }
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu)
+              mv_split2(full + (4 * h + mu) * (9 * LT) + i, LT, va[mu], vb2[mu], pa1, pa2, pb1, pb2);
+          }
+          float2 accA[3], accB[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            accA[c] = make_float2(pa1[c].x - pa2[c].y, pa1[c].y + pa2[c].x);
+            accB[c] = make_float2(pb1[c].x - pb2[c].y, pb1[c].y + pb2[c].x);
+          }
+          const SysF SA = sf32[ja], SB = sf32[jb];
+          if (EPI == EPI_CG_K2) {
+            float2 pA[3], rA[3], xA[3], pB[3], rB[3], xB[3];
+            ld3_rw(a.center, ja, s, Ve, pA);
+            ld3_rw(a.aux, ja, s, Ve, rA);
+            ld3_rw(a.xlo, ja, s, Ve, xA);
+            if (hasB) {
+              ld3_rw(a.center, jb, s, Ve, pB);
+              ld3_rw(a.aux, jb, s, Ve, rB);
+              ld3_rw(a.xlo, jb, s, Ve, xB);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              pA[k] = __ffma2_rn(bc2(SA.beta), pA[k], rA[k]);
+              const float2 ap = __ffma2_rn(bc2(SA.m4), pA[k], make_float2(-accA[k].x, -accA[k].y));
+              rA[k] = __ffma2_rn(bc2(-SA.alpha), ap, rA[k]);
+              xA[k] = __ffma2_rn(bc2(SA.alpha), pA[k], xA[k]);
+              qa0 += rA[k].x * rA[k].x + rA[k].y * rA[k].y;
+              qa1 += rA[k].x * pA[k].x + rA[k].y * pA[k].y;
+            }
+            st3(a.center, ja, s, Ve, pA);
+            st3(a.aux, ja, s, Ve, rA);
+            st3(a.xlo, ja, s, Ve, xA);
+            if (hasB) {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                pB[k] = __ffma2_rn(bc2(SB.beta), pB[k], rB[k]);
+                const float2 ap = __ffma2_rn(bc2(SB.m4), pB[k], make_float2(-accB[k].x, -accB[k].y));
+                rB[k] = __ffma2_rn(bc2(-SB.alpha), ap, rB[k]);
+                xB[k] = __ffma2_rn(bc2(SB.alpha), pB[k], xB[k]);
+                qb0 += rB[k].x * rB[k].x + rB[k].y * rB[k].y;
+                qb1 += rB[k].x * pB[k].x + rB[k].y * pB[k].y;
+              }
+              st3(a.center, jb, s, Ve, pB);
+              st3(a.aux, jb, s, Ve, rB);
+              st3(a.xlo, jb, s, Ve, xB);
+            }
+          } else {
+            float2 tA[3], tB[3];
+            ld3_rw(a.out, ja, s, Ve, tA);
+            if (hasB) ld3_rw(a.out, jb, s, Ve, tB);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              tA[k] = __ffma2_rn(bc2(SA.beta), tA[k], accA[k]);
+              qa0 += tA[k].x * tA[k].x + tA[k].y * tA[k].y;
+            }
+            st3(a.out, ja, s, Ve, tA);
+            if (hasB) {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                tB[k] = __ffma2_rn(bc2(SB.beta), tB[k], accB[k]);
+                qb0 += tB[k].x * tB[k].x + tB[k].y * tB[k].y;
+              }
+              st3(a.out, jb, s, Ve, tB);
+            }
+          }
         }
-        if (EPI == EPI_CG_K2) {
-          ld3_rw(a.center, j, s, Ve, c0);
-          ld3_rw(a.aux, j, s, Ve, c1);
-          ld3_rw(a.xlo, j, s, Ve, c2);
-        } else {
-          ld3_rw(a.out, j, s, Ve, c0);
+        qa0 = warp_sum(qa0);
+        qb0 = warp_sum(qb0);
+        if (NV > 1) {
+          qa1 = warp_sum(qa1);
+          qb1 = warp_sum(qb1);
         }
-        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (EXPAND) {
-          float2 acc2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-          for (int mu = 0; mu < 4; ++mu) {
-            mv_split(full + mu * (9 * LT) + i, LT, vf[mu], acc, acc2);
-            mv_split(full + (4 + mu) * (9 * LT) + i, LT, vb[mu], acc, acc2);
+        if ((tid & 31) == 0) {
+          if (hasA) {
+            red[ja][warp][0] += qa0;
+            if (NV > 1) red[ja][warp][NV - 1] += qa1;
           }
-#pragma unroll
-          for (int a = 0; a < 3; ++a) acc[a] = make_float2(acc[a].x - acc2[a].y, acc[a].y + acc2[a].x);
-        } else {
-#pragma unroll
-          for (int mu = 0; mu < 4; ++mu) {
-            mv_x2(L + mu * (NEL * LT) + i, LT, vf[mu], bf[mu], acc);
-            mvdag_x2(L + (4 + mu) * (NEL * LT) + i, LT, vb[mu], -bb[mu], acc);
+          if (hasB) {
+            red[jb][warp][0] += qb0;
+            if (NV > 1) red[jb][warp][NV - 1] += qb1;
           }
-        }
-        if (EPI == EPI_CG_K2) {
-          // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            c0[k] = __ffma2_rn(bc2(beta), c0[k], c1[k]);
-            const float2 ap = __ffma2_rn(bc2(m4), c0[k], make_float2(-acc[k].x, -acc[k].y));
-            c1[k] = __ffma2_rn(bc2(-alpha), ap, c1[k]);
-            c2[k] = __ffma2_rn(bc2(alpha), c0[k], c2[k]);
-            q0 += c1[k].x * c1[k].x + c1[k].y * c1[k].y;
-            q1 += c1[k].x * c0[k].x + c1[k].y * c0[k].y;
-          }
-          st3(a.center, j, s, Ve, c0);
-          st3(a.aux, j, s, Ve, c1);
-          st3(a.xlo, j, s, Ve, c2);
-        } else {
-          // t = D_oe r + beta t_old
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            c0[k] = __ffma2_rn(bc2(beta), c0[k], acc[k]);
-            q0 += c0[k].x * c0[k].x + c0[k].y * c0[k].y;
-          }
-          st3(a.out, j, s, Ve, c0);
         }
       }
-      q0 = warp_sum(q0);
-      if (NV > 1) q1 = warp_sum(q1);
-      if ((tid & 31) == 0 && has) {
-        red[j][warp][0] += q0;
-        if (NV > 1) red[j][warp][NV - 1] += q1;
+    } else {
+      for (int k0 = 0; k0 < nact; k0 += SL) {
+        const bool has = k0 + lane < nact;  // uniform per warp
+        const int j = has ? act_list[k0 + lane] : 0;
+        const SysF S = sf32[j];
+        const float beta = S.beta, alpha = S.alpha, m4 = S.m4;
+        float q0 = 0.f, q1 = 0.f;
+        if (has && valid) {
+          float2 vf[4][3], vb[4][3], c0[3], c1[3], c2[3];
+  #pragma unroll
+          for (int mu = 0; mu < 4; ++mu) {
+            ld3(a.in, j, sf[mu], Ve, vf[mu]);
+            ld3(a.in, j, sb[mu], Ve, vb[mu]);
+          }
+          if (EPI == EPI_CG_K2) {
+            ld3_rw(a.center, j, s, Ve, c0);
+            ld3_rw(a.aux, j, s, Ve, c1);
+            ld3_rw(a.xlo, j, s, Ve, c2);
+          } else {
+            ld3_rw(a.out, j, s, Ve, c0);
+          }
+          float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          if (EXPAND) {
+            float2 acc2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  #pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+              mv_split(full + mu * (9 * LT) + i, LT, vf[mu], acc, acc2);
+              mv_split(full + (4 + mu) * (9 * LT) + i, LT, vb[mu], acc, acc2);
+            }
+  #pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a] = make_float2(acc[a].x - acc2[a].y, acc[a].y + acc2[a].x);
+          } else {
+  #pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+              mv_x2(L + mu * (NEL * LT) + i, LT, vf[mu], bf[mu], acc);
+              mvdag_x2(L + (4 + mu) * (NEL * LT) + i, LT, vb[mu], -bb[mu], acc);
+            }
+          }
+          if (EPI == EPI_CG_K2) {
+            // p = r + beta p_old; A p = 4 m^2 p - D_eo t; r -= alpha A p; x_lo += alpha p
+  #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              c0[k] = __ffma2_rn(bc2(beta), c0[k], c1[k]);
+              const float2 ap = __ffma2_rn(bc2(m4), c0[k], make_float2(-acc[k].x, -acc[k].y));
+              c1[k] = __ffma2_rn(bc2(-alpha), ap, c1[k]);
+              c2[k] = __ffma2_rn(bc2(alpha), c0[k], c2[k]);
+              q0 += c1[k].x * c1[k].x + c1[k].y * c1[k].y;
+              q1 += c1[k].x * c0[k].x + c1[k].y * c0[k].y;
+            }
+            st3(a.center, j, s, Ve, c0);
+            st3(a.aux, j, s, Ve, c1);
+            st3(a.xlo, j, s, Ve, c2);
+          } else {
+            // t = D_oe r + beta t_old
+  #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              c0[k] = __ffma2_rn(bc2(beta), c0[k], acc[k]);
+              q0 += c0[k].x * c0[k].x + c0[k].y * c0[k].y;
+            }
+            st3(a.out, j, s, Ve, c0);
+          }
+        }
+        q0 = warp_sum(q0);
+        if (NV > 1) q1 = warp_sum(q1);
+        if ((tid & 31) == 0 && has) {
+          red[j][warp][0] += q0;
+          if (NV > 1) red[j][warp][NV - 1] += q1;
+        }
       }
     }
   }
@@ -370,9 +503,9 @@ __global__ void __launch_bounds__(LT * SL, STG == 1 ? 3 : 2) k_cg_nrhs(const DsA
   }
 }
 
-template <int RC_, int EPI_, int SL_, int STG_>
+template <int RC_, int EPI_, int SL_, int STG_, int JJ_>
 static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const void **kptr) {
-  auto k = k_cg_nrhs<RC_, EPI_, SL_, STG_>;
+  auto k = k_cg_nrhs<RC_, EPI_, SL_, STG_, JJ_>;
   const unsigned smem = nrhs_smem_bytes(RC_, STG_);
   static bool attr_set = false;  // benign race: setting it twice is harmless
   if (!attr_set) {
@@ -389,12 +522,18 @@ static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const
 
 cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr) {
-#define STAG_NR(RC_, EPI_, SL_, STG_)                   \
-  if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + SL_) \
-    return nrhs_one<RC_, EPI_, SL_, STG_>(nblocks, st, a, kptr);
-  STAG_NR(0, EPI_CG_K1R, 2, 2) STAG_NR(0, EPI_CG_K2, 2, 2) STAG_NR(1, EPI_CG_K1R, 2, 2) STAG_NR(1, EPI_CG_K2, 2, 2)
-  STAG_NR(0, EPI_CG_K1R, 4, 2) STAG_NR(0, EPI_CG_K2, 4, 2) STAG_NR(1, EPI_CG_K1R, 4, 2) STAG_NR(1, EPI_CG_K2, 4, 2)
-  STAG_NR(1, EPI_CG_K1R, 4, 1) STAG_NR(1, EPI_CG_K2, 4, 1) STAG_NR(0, EPI_CG_K1R, 4, 1) STAG_NR(0, EPI_CG_K2, 4, 1)
+  // form 24: two systems per pass in kernel 1 only -- kernel 2 (three more
+  // vectors per system in its epilogue) measured slower that way and keeps
+  // one system per pass (form 4)
+  if (form == 24 && EPI == EPI_CG_K2) form = 4;
+#define STAG_NR(RC_, EPI_, SL_, STG_, JJ_)                                          \
+  if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + 20 * (JJ_ - 1) + SL_) \
+    return nrhs_one<RC_, EPI_, SL_, STG_, JJ_>(nblocks, st, a, kptr);
+  STAG_NR(0, EPI_CG_K1R, 2, 2, 1) STAG_NR(0, EPI_CG_K2, 2, 2, 1) STAG_NR(1, EPI_CG_K1R, 2, 2, 1)
+  STAG_NR(1, EPI_CG_K2, 2, 2, 1) STAG_NR(0, EPI_CG_K1R, 4, 2, 1) STAG_NR(0, EPI_CG_K2, 4, 2, 1)
+  STAG_NR(1, EPI_CG_K1R, 4, 2, 1) STAG_NR(1, EPI_CG_K2, 4, 2, 1) STAG_NR(1, EPI_CG_K1R, 4, 1, 1)
+  STAG_NR(1, EPI_CG_K2, 4, 1, 1) STAG_NR(0, EPI_CG_K1R, 4, 1, 1) STAG_NR(0, EPI_CG_K2, 4, 1, 1)
+  STAG_NR(1, EPI_CG_K1R, 4, 2, 2)
 #undef STAG_NR
   return cudaErrorNotSupported;
 }

@@ -522,7 +522,8 @@ class Context:
                 "link_path": ("planes", "tiled_smem", "tiled")[f[4]], "l2_persisting_links": f[5] == 1,
                 "l2_persisting": ("none", "links", "vectors")[f[5]],
                 "iterations_per_pass": f[6], "shared_memory_links": bool(f[7]),
-                "kernels": ("k_dslash", "k_dslash_mrhs", "k_cg_nrhs")[f[7]]}
+                "kernels": ("k_dslash", "k_dslash_mrhs", "k_cg_nrhs", "k_cg_nrhs")[f[7]],
+                "k1_systems_per_pass": 2 if f[7] == 3 else 1}
 
     def time_cg_kernel(self, kernel, precision=STAG_FP32, nlaunch=50):
         """(ms per launch, algorithmic bytes per launch) of CG kernel 0 or 1."""

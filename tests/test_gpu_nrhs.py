@@ -4,7 +4,8 @@ oracle and the one-system-per-block form.
 
 Lattices with a ragged last tile (Ve not a multiple of 64), 2..48 systems
 (sources x masses), full and reconstruct-12 links, 2 and 4 threads per site
-with two link stages and 4 with one stage (STAG_NRHS = 2, 4, 14):
+with two link stages, 4 with one stage, and 4 with two systems per pass
+(reconstruct-12; STAG_NRHS = 2, 4, 14, 24):
 every system's true residual recomputed by the oracle is <= 1e-10.
 """
 import os
@@ -45,8 +46,10 @@ def solve_forced(L, U, bs, masses, recon, nrhs):
 
 @pytest.mark.parametrize("L", [(4, 2, 6, 8), (6, 6, 6, 12), (2, 2, 2, 2), (8, 8, 8, 16)])
 @pytest.mark.parametrize("recon", [False, True])
-@pytest.mark.parametrize("sl", [2, 4, 14])
+@pytest.mark.parametrize("sl", [2, 4, 14, 24])
 def test_nrhs_form_matches_oracle(L, recon, sl):
+    if sl == 24 and not recon:
+        pytest.skip("two systems per pass: reconstruct-12 links only")
     V = synth.volume(L)
     U = synth.random_links(L, 0.4, 701)
     bs = [synth.gaussian_vector(V // 2, 702 + r) for r in range(3)]
@@ -70,7 +73,8 @@ def test_nrhs_form_matches_oracle(L, recon, sl):
         assert abs(int(it[j]) - int(it0[j])) <= max(3, int(it0[j]) // 50)
 
 
-def test_nrhs_form_48_systems_production_lattice():
+@pytest.mark.parametrize("sl", [4, 24])
+def test_nrhs_form_48_systems_production_lattice(sl):
     """20^3 x 64, 12 sources x {0.01, 0.02, 0.03, 0.05}: the 48-system batch in
     this form (reconstruct-12 FP32 links), oracle residual of a sample."""
     L = (20, 20, 20, 64)
@@ -79,7 +83,7 @@ def test_nrhs_form_48_systems_production_lattice():
     bs = [synth.gaussian_vector(V // 2, synth.seed_for(2, 100 + r)) for r in range(12)]
     masses = [0.01, 0.02, 0.03, 0.05]
     bd = [torch.from_numpy(b).cuda() for b in bs]
-    xs, st, it, tr, form = solve_forced(L, torch.from_numpy(U).cuda(), bd, masses, True, 4)
+    xs, st, it, tr, form = solve_forced(L, torch.from_numpy(U).cuda(), bd, masses, True, sl)
     torch.cuda.synchronize()
     assert st == stag.STAG_OK and np.all(tr <= 1e-10)
     assert form["kernels"] == "k_cg_nrhs"
