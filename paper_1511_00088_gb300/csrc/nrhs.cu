@@ -538,6 +538,6 @@ cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream
   return cudaErrorNotSupported;
 }
 
-unsigned cg_nrhs_smem(int recon, int form) { return nrhs_smem_bytes(recon, form >= 10 ? 1 : 2); }
+unsigned cg_nrhs_smem(int recon, int form) { return nrhs_smem_bytes(recon, form == 14 ? 1 : 2); }
 
 }  // namespace stag
