@@ -536,7 +536,8 @@ int nrhs_blocks(stag_ctx *c, int recon, int sl, int EPI, int *nb) {
   const void *k = nullptr;
   CK(launch_cg_nrhs(recon, sl, EPI, 0, c->stream, none, &k));
   int per_sm = 0, nsm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * (sl % 10), cg_nrhs_smem(recon, sl)));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LT * (sl % 10),
+                                                   cg_nrhs_smem(recon, nrhs_kernel_form(sl, EPI))));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   int n = per_sm * nsm;
   if (n < 1) n = 1;

@@ -96,6 +96,7 @@ cudaError_t launch_dslash_mrhs(int LP, int recon, int nsw, int EPI, int nblocks,
 cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr = nullptr);
 unsigned cg_nrhs_smem(int recon, int form);
+int nrhs_kernel_form(int form, int EPI);
 constexpr int CG_NRHS_MAX = 64;
 
 cudaError_t launch_accum_x(int RP, int NS, int nblocks, cudaStream_t st, const BlasArgs &a);

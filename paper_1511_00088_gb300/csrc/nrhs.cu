@@ -520,12 +520,14 @@ static cudaError_t nrhs_one(int nblocks, cudaStream_t st, const DsArgs &a, const
   return launch_ex_full(k, nblocks, LT * SL_, smem, st, a.pdl != 0, a.l2_base, a.l2_bytes, a.l2_hit, a);
 }
 
+// The form each kernel of a mixed form runs.  Form 24: two systems per pass
+// in kernel 1 only -- kernel 2 (three more vectors per system in its
+// epilogue) measured slower that way and keeps one system per pass (form 4).
+int nrhs_kernel_form(int form, int EPI) { return (EPI == EPI_CG_K2 && form == 24) ? 4 : form; }
+
 cudaError_t launch_cg_nrhs(int recon, int form, int EPI, int nblocks, cudaStream_t st, const DsArgs &a,
                            const void **kptr) {
-  // form 24: two systems per pass in kernel 1 only -- kernel 2 (three more
-  // vectors per system in its epilogue) measured slower that way and keeps
-  // one system per pass (form 4)
-  if (form == 24 && EPI == EPI_CG_K2) form = 4;
+  form = nrhs_kernel_form(form, EPI);
 #define STAG_NR(RC_, EPI_, SL_, STG_, JJ_)                                          \
   if (recon == RC_ && EPI == EPI_ && form == 10 * (2 - STG_) + 20 * (JJ_ - 1) + SL_) \
     return nrhs_one<RC_, EPI_, SL_, STG_, JJ_>(nblocks, st, a, kptr);
