@@ -253,7 +253,9 @@ int stag_solve_full(stag_ctx *ctx, const double *const src[], int nrhs, const do
  * on the context stream over `nlaunch` pairs of the two kernels launched
  * alternately, as the iteration runs them (each starts on the cache state the
  * other leaves), on the context's own internal vectors with the solver's
- * launch configuration:
+ * launch configuration, including (single-system forms) the reduction of the
+ * other kernel's partial sums that every block of a CG kernel finishes
+ * before its own work in the solve:
  *   kernel 0: t = D_oe r + beta t_old (FP32/FP64 Krylov vectors) or
  *             t = D_oe (r + beta p_old) (STAG_HALF_VECTORS), with |t|^2;
  *   kernel 1: p = r + beta p_old, r -= alpha (4 m^2 p - D_eo t),

@@ -2381,6 +2381,28 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   a2.par_out = 0;
   a2.in = w.t.arg();
   a2.center = w.p.arg();
+  // As in the solve's folded loop, each kernel first finishes its
+  // predecessor's reduction in every block (fold_state over the other
+  // kernel's partials, states double-buffered); GATE_NONE keeps every system
+  // processed whatever the (zeroed, meaningless) states say, so the timing
+  // holds the fold's reads and arithmetic and the whole kernel body.
+  const bool folded = c->fold && !w.nrhs_sl;
+  SysState *S[2] = {(SysState *)w.st.p, (SysState *)w.st2.p};
+  double *PA = (double *)w.partials.p, *PB = (double *)w.partials2.p;
+  const bool rec1 = (w.VP == w.RP);
+  int cur = 0;
+  auto prep = [&](int k) {
+    if (!folded) return;
+    DsArgs &x = k == 0 ? a1 : a2;
+    x.ctl.st = S[cur];
+    x.ctl.partials = k == 0 ? PA : PB;
+    x.fold = k == 0 ? FIN_NORM : (rec1 ? FIN_ALPHA_R : FIN_ALPHA);
+    x.fold_partials = k == 0 ? PB : PA;
+    x.fold_nbx = k == 0 ? w.nbx_k2 : w.nbx_k1;
+    x.fold_nv = (k == 0 || !rec1) ? 2 : 1;
+    x.st_out = S[1 - cur];
+    cur = 1 - cur;
+  };
   // alternate them as the iteration does (so each starts with the cache the
   // other leaves), an event between every two launches
   std::vector<cudaEvent_t> ev(2 * (size_t)nlaunch + 1, nullptr);
@@ -2388,17 +2410,23 @@ int stag_time_cg_kernel(stag_ctx *c, int precision, int kernel, int nlaunch, dou
   for (auto &e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) st = fail(c, STAG_ERR_CUDA, "cudaEventCreate", cudaGetLastError());
   for (int i = 0; i < 2 && st == STAG_OK; ++i) {  // warm-up pair
-    if (launch_cg(c, 0, epi1, c->stream, a1) != cudaSuccess || launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess)
+    prep(0);
+    if (launch_cg(c, 0, epi1, c->stream, a1) != cudaSuccess) st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
+    prep(1);
+    if (st == STAG_OK && launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess)
       st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
   }
   if (w.l2p) l2_setaside(c, true);
   if (st == STAG_OK && cudaEventRecord(ev[0], c->stream) != cudaSuccess)
     st = fail(c, STAG_ERR_CUDA, "cudaEventRecord", cudaGetLastError());
   for (int i = 0; i < nlaunch && st == STAG_OK; ++i) {
+    prep(0);
     if (launch_cg(c, 0, epi1, c->stream, a1) != cudaSuccess ||
-        cudaEventRecord(ev[2 * i + 1], c->stream) != cudaSuccess ||
-        launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess ||
-        cudaEventRecord(ev[2 * i + 2], c->stream) != cudaSuccess)
+        cudaEventRecord(ev[2 * i + 1], c->stream) != cudaSuccess)
+      st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
+    prep(1);
+    if (st == STAG_OK && (launch_cg(c, 1, EPI_CG_K2, c->stream, a2) != cudaSuccess ||
+                          cudaEventRecord(ev[2 * i + 2], c->stream) != cudaSuccess))
       st = fail(c, STAG_ERR_CUDA, "launch", cudaGetLastError());
   }
   double tot = 0.0;
