@@ -255,7 +255,11 @@ int stag_solve_full(stag_ctx *ctx, const double *const src[], int nrhs, const do
  * other leaves), on the context's own internal vectors with the solver's
  * launch configuration, including (single-system forms) the reduction of the
  * other kernel's partial sums that every block of a CG kernel finishes
- * before its own work in the solve:
+ * before its own work in the solve.  With programmatic dependent launch on
+ * (the default), an event between two launches would stop the overlap of a
+ * kernel's launch with its predecessor's tail that the solve has, so the
+ * pairs are also timed with events only around the whole sequence and each
+ * kernel is given its share, from the separated timings, of that pair time:
  *   kernel 0: t = D_oe r + beta t_old (FP32/FP64 Krylov vectors) or
  *             t = D_oe (r + beta p_old) (STAG_HALF_VECTORS), with |t|^2;
  *   kernel 1: p = r + beta p_old, r -= alpha (4 m^2 p - D_eo t),
